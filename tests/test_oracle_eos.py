@@ -1,0 +1,111 @@
+"""Pins of the oracle's equations of state and coexistence solvers against
+closed forms (van der Waals critical point), an independent thermodynamic
+route (equal chemical potential instead of equal area), finite differences,
+and the densities the paper prints in Table 1."""
+import math
+import warnings
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import analysis as An
+
+warnings.filterwarnings("ignore", category=Warning, module="scipy")
+
+CS = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
+VDW = O.Params(eos=O.EOS_VDW, a=9 / 49, b=2 / 21, R=1.0, K=0.3, A=-0.5)
+
+
+def test_c_and_python_eos_agree():
+    for base, rhos in ((CS, np.linspace(0.001, 0.6, 50)), (VDW, np.linspace(0.1, 9.0, 50))):
+        p = An.with_T(base, 0.08 if base is CS else 0.5)
+        np.testing.assert_allclose(O.pressure(p, rhos), An.p_eos(p, rhos), rtol=1e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("eos", ["cs", "vdw", "pr"])
+def test_analytic_derivative_matches_finite_difference(eos):
+    if eos == "cs":
+        p, rhos = An.with_T(CS, 0.07), np.linspace(0.01, 0.5, 13)
+    elif eos == "vdw":
+        p, rhos = An.with_T(VDW, 0.5), np.linspace(0.2, 8.0, 13)
+    else:
+        p = O.Params(eos=O.EOS_PR, a=2 / 49, b=2 / 21, R=1.0, K=0.5, omega=0.344, Tc=0.0729, T=0.058)
+        rhos = np.linspace(0.2, 8.0, 13)
+    h = 1e-6
+    fd = (An.p_eos(p, rhos + h) - An.p_eos(p, rhos - h)) / (2 * h)
+    np.testing.assert_allclose(An.dp_drho(p, rhos), fd, rtol=1e-7, atol=1e-9)
+
+
+def test_vdw_critical_point_closed_form():
+    rc, Tc, pc = An.critical_point(VDW)
+    a, b, R = VDW.a, VDW.b, VDW.R
+    assert abs(Tc - 8 * a / (27 * b * R)) < 1e-12          # = 4/7
+    assert abs(rc - 1 / (3 * b)) < 1e-6                     # = 3.5
+    assert abs(pc - VDW.K * a / (27 * b * b)) < 1e-9
+
+
+def test_cs_critical_point_is_an_inflection_with_zero_slope():
+    rc, Tc, pc = An.critical_point(CS)
+    p = An.with_T(CS, Tc)
+    h = 1e-4
+    d1 = float(An.dp_drho(p, rc))
+    d2 = float((An.dp_drho(p, rc + h) - An.dp_drho(p, rc - h)) / (2 * h))
+    assert abs(d1) < 1e-12 and abs(d2) < 1e-6  # p'' ~ 1 here; rho_c is found to ~1e-7
+    # the usual Carnahan-Starling constants T_c = 0.3773 a/(b R), rho_c = 0.5218/b
+    assert abs(Tc - 0.3773 / 4) < 1e-4 and abs(rc - 0.5218 / 4) < 1e-4
+
+
+def _mu(p, rho):
+    """Chemical potential up to a constant, from its closed form (not from
+    the equal-area integral): d mu / d rho = (dp/drho) / rho."""
+    RT = p.R * p.T
+    if p.eos == O.EOS_VDW:
+        return p.K * (RT * math.log(rho / (1 - p.b * rho)) + RT * p.b * rho / (1 - p.b * rho)
+                      - 2 * p.a * rho)
+    eta = p.b * rho / 4
+    return p.K * (RT * (math.log(rho) + (8 * eta - 9 * eta**2 + 3 * eta**3) / (1 - eta) ** 3)
+                  - 2 * p.a * rho)
+
+
+@pytest.mark.parametrize("base,tr", [(CS, 0.6), (CS, 0.7), (CS, 0.8), (VDW, 0.9)])
+def test_maxwell_coexistence_has_equal_pressure_and_chemical_potential(base, tr):
+    _, Tc, _ = An.critical_point(base)
+    p = An.with_T(base, tr * Tc)
+    rg, rl, p0 = An.maxwell(p)
+    assert rg < rl
+    assert abs(float(An.p_eos(p, rg)) - p0) < 1e-12 * max(p0, 1e-3)
+    assert abs(float(An.p_eos(p, rl)) - p0) < 1e-12 * max(p0, 1e-3)
+    assert abs(_mu(p, rg) - _mu(p, rl)) < 1e-9 * abs(_mu(p, rl))
+
+
+def test_mechanical_stability_reproduces_table1(golden):
+    """Eq. 17 with eps = -2A (R9), c = 1 (R7), K on the whole EOS (R8)
+    lands on Table 1's printed densities within 4e-4."""
+    _, Tc, _ = An.critical_point(VDW)
+    p = An.with_T(VDW, 0.9 * Tc)
+    rg, rl, _ = An.mechanical_stability(p)
+    t1 = golden["table1_flat_interface"]
+    assert abs(rl / t1["rho_l"] - 1) < 1e-4
+    assert abs(rg / t1["rho_g"] - 1) < 4e-4
+    # other eps readings do not match (they are off by > 5 %)
+    for eps in (0.0, -1.0):
+        alt = An.mechanical_stability(p, eps=eps)
+        assert alt is None or abs(alt[0] / t1["rho_g"] - 1) > 0.05
+
+
+def test_eq17_has_no_positive_pressure_coexistence_for_cs_at_0p7_with_small_A():
+    """With A = -0.152 (eps = 0.304) the Carnahan-Starling law at 0.7 T_c has
+    no Eq. 17 coexistence with p0 > 0; with A = -0.85 its liquid density is
+    within 0.2 % and its gas density within 15 % of Maxwell's at 0.6, 0.7 and
+    0.8 T_c (reading R-A)."""
+    _, Tc, _ = An.critical_point(CS)
+    p = An.with_T(CS, 0.7 * Tc)
+    p.A = -0.152
+    assert An.mechanical_stability(p) is None
+    for tr in (0.6, 0.7, 0.8):
+        q = An.with_T(CS, tr * Tc)
+        q.A = -0.85
+        rg, rl, _ = An.mechanical_stability(q)
+        mg, ml, _ = An.maxwell(q)
+        assert abs(rl / ml - 1) < 2e-3 and abs(rg / mg - 1) < 0.15
