@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Throughput of the fused sm_103a pseudo-potential MRT step (MLUPS and
+fraction of the HBM roofline), FP32 deviation storage with FP64 beside it.
+
+Workload: spinodal decomposition on one 4096 x 4096 periodic lattice,
+rho0 = 0.25 (1 + 0.01 u), u from splitmix64 (seed 14127228),
+Carnahan-Starling (a=1, b=4, R=1) at T = 0.7 Tc, A = -0.85, kappa = 0.3,
+s = (1, 1.1, 1.1, 1, 1.1, 1, 1.1, 1, 1).  One step = one fused kernel
+launch over the whole lattice (density, psi, force, Q, collision, stream).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference implementation
+of this method here) on the host cores, one step = one oracle time step on a
+256 x 256 periodic sample of the same workload.  Under torchrun (N > 1) each
+rank runs its own replica lattice (the method needs no exchange between
+independent lattices); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline, FP32 vs FP64 on one GB300, sigma err <= 1e-3"
+SEED = 14127228
+S_CFG = [1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0]
+A_CFG, KAPPA_CFG, TR_CFG, RHO0 = -0.85, 0.3, 0.7, 0.25
+PEAK_FALLBACK_GBS = 6800.0
+
+
+def workload_config(nx, ny, precision, extra=None):
+    cfg = {
+        "workload": "spinodal decomposition %dx%d periodic, Carnahan-Starling a=1 b=4 R=1, T=0.7Tc, "
+                    "A=-0.85, kappa=0.3, rho0=0.25(1+0.01u)" % (nx, ny),
+        "nx": nx, "ny": ny, "precision": precision,
+        "l2": "inputs larger than L2: two %.0f MB population arrays per step" % (
+            9 * nx * ny * (4 if precision == "fp32" else 8) / 1e6),
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+def kernel_traffic(prec_name):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    src = os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", "lbm_step.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "step_%s_4096_traffic.txt" % prec_name)
+    try:
+        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line)
+    except OSError:
+        return None
+    if kv.get("lbm_step_cu_sha256_16") != sha:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        rows = []
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[4]),
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        load = [r for r in rows if r["util"] > 0] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in load),
+                "reasons": sorted(reasons), "samples": len(load)}
+
+
+def make_lattice(P, nx, ny, prec, rho0, stream=None):
+    eos = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
+    _, Tc, _ = P.lbm_eos_critical(eos)
+    eos.T = TR_CFG * Tc
+    lat = P.Lattice(nx, ny, prec, stream=stream)
+    lat.set_params(eos, A_CFG, KAPPA_CFG, G=-1.0, s=S_CFG, rho_ref=RHO0)
+    lat.init_density(rho0)
+    return lat
+
+
+def time_steps(torch, lat, steps):
+    st = lat.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    lat.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def cpu_oracle_mlups(nx, ny, steps):
+    """The FP64 oracle as it stands, single-threaded, on a periodic nx x ny
+    sample of the workload."""
+    import warnings
+    warnings.filterwarnings("ignore")
+    import lbm_inputs as I
+    import oracle as O
+    from oracle import analysis as An
+    base = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, A=A_CFG, kappa=KAPPA_CFG, G=-1.0, s=list(S_CFG))
+    _, Tc, _ = An.critical_point(base)
+    p = An.with_T(base, TR_CFG * Tc)
+    f = O.init_equilibrium(I.spinodal_density(nx, ny, RHO0, 0.01, SEED))
+    O.step(p, f, 1)
+    t0 = time.perf_counter()
+    O.step(p, f, steps)
+    dt = time.perf_counter() - t0
+    return nx * ny * steps / dt / 1e6, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import warnings
+    warnings.filterwarnings("ignore")
+    import lbm_inputs as I
+    import oracle as O
+    from oracle import analysis as An
+    n = 256
+    base = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, A=A_CFG, kappa=KAPPA_CFG, G=-1.0, s=list(S_CFG))
+    _, Tc, _ = An.critical_point(base)
+    p = An.with_T(base, TR_CFG * Tc)
+    f = O.init_equilibrium(I.spinodal_density(n, n, RHO0, 0.01, SEED))
+    O.step(p, f, args.warmup)
+    t0 = time.perf_counter()
+    O.step(p, f, args.steps)
+    dt = time.perf_counter() - t0
+    mlups = n * n * args.steps / dt / 1e6
+    sample = "%dx%d periodic sample of the workload per step, FP64 oracle, single thread" % (n, n)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1000.0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.nx, args.ny, "fp64", {"sample": "%dx%d" % (n, n)}),
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import lbm_inputs as I
+    import paper_1412_7228_gb300 as P
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    nx, ny = args.nx, args.ny
+    N = nx * ny
+    rho0 = I.spinodal_density(nx, ny, RHO0, 0.01, SEED)
+
+    lat = make_lattice(P, nx, ny, P.LBM_FP32, rho0)
+    tile = None
+    if args.autotune:
+        k, s, ms = lat.autotune(10)
+        tile = P.lbm_tile_configs(P.LBM_FP32)[k]
+    else:
+        tile = P.lbm_tile_configs(P.LBM_FP32)[0]
+    lat.use_graphs(True)
+    launches0 = lat.kernel_launches
+    lat.step(args.warmup)
+    lat.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    with ClockSampler(local) as clk:
+        barrier()
+        launches_t0 = lat.kernel_launches
+        t = time_steps(torch, lat, args.steps)
+        barrier()
+    launches = lat.kernel_launches - launches_t0
+    status_ok = True
+    try:
+        lat.sync()
+    except P.LbmError:
+        status_ok = False
+    if dist is not None:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    mlups = ws * N * args.steps / t / 1e6
+    avg_launch = t / args.steps
+    peak, peak_kind = measured_peak()
+    bpu = 72
+    achieved = bpu * N / avg_launch / 1e9
+    traffic = kernel_traffic("fp32")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": bpu,
+            "kernel": "lbm::k_step<float,%d,%d,%d>" % tuple(tile)}
+    lat.close()
+
+    # ---- FP64 on the same workload (fewer steps: it is FP64-ALU bound) ----
+    fp64 = None
+    if not args.no_fp64:
+        lat64 = make_lattice(P, nx, ny, P.LBM_FP64, rho0)
+        lat64.use_graphs(True)
+        lat64.step(min(args.warmup, 10))
+        lat64.sync()
+        k64 = max(32, args.steps // 8)
+        t64 = time_steps(torch, lat64, k64)
+        lat64.sync()
+        m64 = N * k64 / t64 / 1e6
+        fp64 = {"value": m64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1000.0,
+                "hbm_frac": 144 * N / (t64 / k64) / 1e9 / peak, "bytes_per_update": 144}
+        lat64.close()
+
+    # ---- end to end through the public API with host buffers -------------
+    e2e = None
+    if not args.no_e2e:
+        host_rho = torch.from_numpy(rho0).pin_memory().numpy()
+        out_rho = torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy()
+        eos = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
+        _, Tc, _ = P.lbm_eos_critical(eos)
+        eos.T = TR_CFG * Tc
+        lat = P.Lattice(nx, ny, P.LBM_FP32)
+        lat.set_params(eos, A_CFG, KAPPA_CFG, G=-1.0, s=S_CFG, rho_ref=RHO0)
+        lat.use_graphs(True)
+        lat.init_density(host_rho)
+        lat.step(args.warmup)
+        lat.sync()
+        barrier()
+        t0 = time.perf_counter()
+        lat.init_density(host_rho)
+        lat.step(args.steps)
+        out = lat.read_fields(which=("rho",))["rho"]
+        out_rho[...] = out
+        t_e2e = time.perf_counter() - t0
+        lat.close()
+        e2e = {"value": N * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * N / args.steps, "d2h_bytes_per_step": 8 * N / args.steps,
+               "what": "lbm_init_density from pinned host rho, lbm_step(K), lbm_read_fields(rho) to host"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cn = args.cpu_n
+        m, dt = cpu_oracle_mlups(cn, cn, args.cpu_steps)
+        cpu = {"value": m, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "%d steps of a %dx%d periodic sample of the workload (%.1f s), FP64 single-thread"
+                         % (args.cpu_steps, cn, cn, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1000.0 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(nx, ny, "fp32", {"tile": list(tile), "graphs": True,
+                                                       "parallelism": "replicas" if ws > 1 else "single"}),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches, "fp64": fp64, "status_ok": status_ok,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nx", type=int, default=4096)
+    ap.add_argument("--ny", type=int, default=4096)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=2048)
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

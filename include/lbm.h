@@ -1,0 +1,214 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) pseudo-potential lattice Boltzmann
+ * library: the per-timestep D2Q9 MRT update of Kupershtokh et al.'s hybrid
+ * pseudo-potential model with the kappa-scaled pressure-tensor modification
+ * of Hu, Li & Uddin, "Surface tension adjustment in a pseudo-potential
+ * lattice Boltzmann model" (arXiv:1412.7228), Sections 2 and 3.2.
+ *
+ * Conventions shared by every call
+ *  - Every call returns an int: LBM_OK (0) or a negative LBM_E* code; the
+ *    message of the last failure is lbm_last_error(ctx).
+ *  - Fields are row-major with x fastest: node (x, y) is element y*nx + x of
+ *    a host array of nx*ny doubles.  Lattice velocities e_0..e_8 are (0,0),
+ *    (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
+ *  - Moment order of Eq. 4: (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy);
+ *    s[9] is the diagonal of Lambda (Eq. 2) in that order.
+ *  - Host pointers belong to the caller and are only read or written during
+ *    the call.  Device memory belongs to the context, unless the caller hands
+ *    in dev_buf, which the library then uses but never frees.
+ *  - Work is enqueued on the context's CUDA stream.  lbm_step() is
+ *    asynchronous; every call that returns data to the host synchronises the
+ *    stream.  Device-side faults of the method (a density outside the EOS's
+ *    psi domain, NaN, a bounded wait that gave up) set a sticky per-instance
+ *    status that the next synchronising call returns as LBM_EUNSTABLE or
+ *    LBM_ETIMEOUT.
+ *  - A context holds one or more independent lattices ("instances"); the
+ *    single-lattice calls act on instance 0, the lbm_batch_* calls on
+ *    instance i, and lbm_step() advances every instance.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* bad argument; nothing was done */
+#define LBM_ENOMEM (-2)    /* device buffer too small or allocation failed */
+#define LBM_ECUDA (-3)     /* a CUDA runtime call failed */
+#define LBM_EUNSTABLE (-4) /* sticky: a density left the psi domain or became NaN */
+#define LBM_ETIMEOUT (-5)  /* sticky: a bounded device wait gave up */
+#define LBM_EIO (-6)       /* checkpoint file could not be read or written */
+
+/* Storage precision of the populations. */
+#define LBM_FP32 1 /* FP32, stored as deviations f_a - t_a rho_ref */
+#define LBM_FP64 2 /* FP64 */
+
+/* Equations of state (the pressure law that sets psi through Eq. 10). */
+#define LBM_EOS_CS 1  /* Carnahan-Starling: K(rho R T (1+n+n^2-n^3)/(1-n)^3 - a rho^2), n = b rho/4 */
+#define LBM_EOS_VDW 2 /* van der Waals, Eq. 21: K(rho R T/(1 - b rho) - a rho^2) */
+#define LBM_EOS_PR 3  /* Peng-Robinson, Eq. 29, with alpha(T) from omega and Tc */
+
+/* Flags of lbm_set_params. */
+#define LBM_FLAG_LI_EPS 0x1u /* third entry of C (Eq. 26) = -1.5 s_eps (Q_xx+Q_yy), Li et al.'s form */
+/* Test hook: every CTA of the next steps also waits on a barrier phase that
+ * nothing completes, with a 2 ms limit, and then reports LBM_ETIMEOUT. */
+#define LBM_FLAG_TEST_FORCE_TIMEOUT 0x100u
+
+/* Number of doubles written by lbm_batch_measure. */
+#define LBM_MEASURE_N 8
+
+typedef struct {
+    int kind;      /* LBM_EOS_* */
+    double a, b, R; /* EOS constants */
+    double K;      /* scale of the whole law (Section 3, Eq. 21) */
+    double T;      /* absolute temperature */
+    double omega;  /* Peng-Robinson acentric factor (Eq. 29); else ignored */
+    double Tc;     /* Peng-Robinson critical temperature in alpha(T); else ignored */
+} lbm_eos;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* ---- Host-side EOS helpers (no GPU needed) ---------------------------- */
+
+/* p_EOS(rho) of the law (Eq. 21, Eq. 29 or Carnahan-Starling). */
+int lbm_eos_pressure(const lbm_eos* eos, double rho, double* p);
+
+/* Critical point (rho_c, T_c, p_c) of the law, found numerically as the
+ * temperature where min_rho dp/drho reaches 0; eos->T is ignored.  Used to
+ * express temperatures as T/T_c (Section 3). */
+int lbm_eos_critical(const lbm_eos* eos, double* rho_c, double* T_c, double* p_c);
+
+/* Maxwell equal-area coexistence at eos->T: densities rho_g < rho_l and the
+ * coexistence pressure p0.  Used to build initial droplet and slab fields.
+ * LBM_EINVAL when eos->T is not below T_c. */
+int lbm_eos_maxwell(const lbm_eos* eos, double* rho_g, double* rho_l, double* p0);
+
+/* Least-squares line through (1/R_i, dp_i), Laplace's law Eq. 22:
+ * dp = sigma / R + icpt; r2 is the coefficient of determination.  n >= 2. */
+int lbm_laplace_fit(int n, const double* dp, const double* R, double* sigma, double* icpt,
+                    double* r2);
+
+/* ---- Context ------------------------------------------------------------ */
+
+/* Bytes of device memory one context of these lattices needs when the caller
+ * supplies dev_buf (populations of two time levels with their ghost layers,
+ * per-instance descriptors, tile table, reduction and field scratch).
+ * 0 on bad arguments (n < 1, any nx or ny < 2, unknown precision). */
+size_t lbm_required_bytes(int nx, int ny, int precision);
+size_t lbm_batch_required_bytes(int n, const int* nx, const int* ny, int precision);
+
+/* Create a context of one nx x ny periodic lattice (lbm_create) or of n
+ * independent lattices (lbm_batch_create) in the given precision.
+ * dev_buf: caller-owned device memory of at least the required bytes, 256-byte
+ * aligned, or NULL to let the library allocate (and later free) its own.
+ * stream: a cudaStream_t, or NULL for the legacy default stream.  Binds the
+ * context to the calling thread's current device.  Parameters must be set
+ * and a density initialised before the first lbm_step. */
+int lbm_create(lbm_ctx** out, int nx, int ny, int precision, void* dev_buf, size_t buf_bytes,
+               void* stream);
+int lbm_batch_create(lbm_ctx** out, int n, const int* nx, const int* ny, int precision,
+                     void* dev_buf, size_t buf_bytes, void* stream);
+
+/* Release everything the context allocated (not a caller-owned dev_buf). */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Model parameters (Sections 2-3): EOS, hybrid-force weight A of Eq. 9,
+ * surface-tension parameter kappa of Eq. 23, interaction strength G (only
+ * its sign matters; G = 0 switches the interaction force and Q off),
+ * relaxation rates s[9] (Eq. 2, moment order), the reference density rho_ref
+ * subtracted from the FP32 populations, and LBM_FLAG_* flags. */
+int lbm_set_params(lbm_ctx* ctx, const lbm_eos* eos, double A, double kappa, double G,
+                   const double s[9], double rho_ref, unsigned flags);
+int lbm_batch_set_params(lbm_ctx* ctx, int i, const lbm_eos* eos, double A, double kappa,
+                         double G, const double s[9], double rho_ref, unsigned flags);
+
+/* Initial state f_a = M^-1 m_eq(rho, u) (Eq. 4) from host fields of nx*ny
+ * doubles; ux, uy may be NULL (zero velocity).  Resets the step counter and
+ * the instance's status. */
+int lbm_init_density(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
+int lbm_batch_init_density(lbm_ctx* ctx, int i, const double* rho, const double* ux,
+                           const double* uy);
+
+/* Enqueue n time steps (Eqs. 1, 9, 10, 23, 25, 26: density and psi, hybrid
+ * force, modifying tensor, moment-space collision, streaming) of every
+ * instance; one fused kernel launch per step, replayed from a CUDA graph
+ * when graphs are on.  Asynchronous. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Wait for the stream; return the first sticky status of any instance. */
+int lbm_sync(lbm_ctx* ctx);
+/* Sticky status of instance i (synchronises). */
+int lbm_status(lbm_ctx* ctx, int i);
+/* Clear every instance's sticky status. */
+int lbm_clear_status(lbm_ctx* ctx);
+
+/* Macroscopic fields of the current state, each nx*ny doubles, any may be
+ * NULL: rho = sum f, u = (sum f e + F/2)/rho (F of Eq. 9), psi of Eq. 10. */
+int lbm_read_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* psi);
+int lbm_batch_read_fields(lbm_ctx* ctx, int i, double* rho, double* ux, double* uy,
+                          double* psi);
+
+/* Pre-collision populations f_a(x, t) as 9*nx*ny doubles, index a*nx*ny + y*nx + x. */
+int lbm_read_populations(lbm_ctx* ctx, double* f);
+int lbm_batch_read_populations(lbm_ctx* ctx, int i, double* f);
+
+/* Laplace-law sampling (Eq. 22) of a droplet centred at (cx, cy): mean
+ * pressure p = p_EOS(rho) = rho/3 + G psi^2/2 (Eq. 10) over nodes within
+ * r_in and beyond r_out (periodic minimum image), and the equimolar radius
+ * R_eq = sqrt((sum rho - rho_out N)/(pi (rho_in - rho_out))).  Sums are FP64. */
+int lbm_measure_pressure_jump(lbm_ctx* ctx, double cx, double cy, double r_in, double r_out,
+                              double* p_in, double* p_out, double* R_eq);
+/* Same for instance i; out[LBM_MEASURE_N] = {p_in, p_out, rho_in, rho_out,
+ * R_eq, mass, n_in, n_out}. */
+int lbm_batch_measure(lbm_ctx* ctx, int i, double cx, double cy, double r_in, double r_out,
+                      double* out);
+
+/* FP64 totals of the current state: mass sum rho, momentum sum rho u,
+ * kinetic energy sum rho |u|^2 / 2, and max |u| (the peak spurious velocity
+ * of a static droplet). */
+int lbm_stats(lbm_ctx* ctx, double* mass, double* mom_x, double* mom_y, double* ke,
+              double* umax);
+int lbm_batch_stats(lbm_ctx* ctx, int i, double* out5);
+
+/* Checkpoint: a header (sizes, precision, parameters, step count) and the
+ * populations of every instance.  lbm_load needs a context of the same
+ * shapes and precision and restores parameters, state and step count. */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Tile configurations of the fused step kernel for this precision: returns
+ * their number; for index k writes tile width, height and threads per CTA. */
+int lbm_tile_config_count(int precision);
+int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads);
+/* Select tile configuration k and CTA schedule (0: instance-major row
+ * order, 1: tiles of all instances interleaved, 2: largest instance first). */
+int lbm_set_schedule(lbm_ctx* ctx, int tile_config, int schedule);
+/* Time every (tile configuration, schedule) pair over `steps` steps of the
+ * current state (which is restored afterwards) and keep the fastest.
+ * Writes the choice and its time per step in milliseconds. */
+int lbm_autotune(lbm_ctx* ctx, int steps, int* tile_config, int* schedule, double* ms_per_step);
+
+/* CUDA graphs for lbm_step: on (1) or off (0, the default). */
+int lbm_use_graphs(lbm_ctx* ctx, int on);
+
+/* Steps done since the last init/load, and fused-step kernel launches
+ * (graph replays count every kernel in them) since creation. */
+long long lbm_steps_done(lbm_ctx* ctx);
+long long lbm_kernel_launches(lbm_ctx* ctx);
+
+/* Algorithmic bytes one lattice update moves: 9 population reads and 9
+ * writes (72 for FP32, 144 for FP64). */
+int lbm_bytes_per_update(int precision);
+
+const char* lbm_last_error(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

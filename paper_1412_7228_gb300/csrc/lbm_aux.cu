@@ -1,0 +1,317 @@
+// lbm_aux.cu -- kernels around the fused step: initial equilibrium, ghost
+// images, read-back of populations and macroscopic fields, and the FP64
+// reductions behind Laplace's law (Eq. 22) and the run statistics.
+// None of these is on the per-step path.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Lattice weights t_a of the D2Q9 equilibrium (4/9, 1/9, 1/36).
+__device__ __forceinline__ double tw(int a) { return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+template <typename T> __device__ __forceinline__ T* popk(const Inst* I, int parity) {
+    return static_cast<T*>(I->pop[parity]);
+}
+
+// Element (a, x, y) of a time level; x in [-GX, pitch-GX), y in [-2, ny+2).
+template <typename T> __device__ __forceinline__ long long at(const Inst* I, int a, int x, int y) {
+    return a * I->plane + static_cast<long long>(y + GY) * I->pitch + (x + Prec<T>::GX);
+}
+
+// ---- initial state: f_a(z) = f_eq,a(rho(z), u(z)); pull storage keeps it at z - e_a
+template <typename T>
+__global__ void k_init(const Inst* __restrict__ I, const double* __restrict__ rho, const double* __restrict__ ux,
+                       const double* __restrict__ uy, int parity) {
+    const int nx = I->nx, ny = I->ny;
+    const long long N = static_cast<long long>(nx) * ny;
+    T* p = popk<T>(I, parity);
+    const double rr = static_cast<double>(phys<T>(I).rho_ref);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % nx), y = static_cast<int>(i / nx);
+        const double r = rho[i], u = ux ? ux[i] : 0.0, v = uy ? uy[i] : 0.0;
+        const double u2 = u * u + v * v;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const double eu = cx(a) * u + cy(a) * v;
+            // textbook second-order equilibrium, minus t_a rho_ref
+            const double dev = tw(a) * ((r - rr) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * u2));
+            int xs = x - cx(a), ys = y - cy(a);
+            xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+            ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+            p[at<T>(I, a, xs, ys)] = static_cast<T>(dev);
+        }
+    }
+}
+
+// Ghost cells x in [-2,0) U [nx,nx+2), y in [-2,0) U [ny,ny+2) of every plane.
+template <typename T> __global__ void k_ghosts(const Inst* __restrict__ I, int parity) {
+    const int nx = I->nx, ny = I->ny;
+    const int W = nx + 4, H = ny + 4;
+    const long long M = static_cast<long long>(W) * H * 9;
+    T* p = popk<T>(I, parity);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < M;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int a = static_cast<int>(i / (static_cast<long long>(W) * H));
+        const long long r = i % (static_cast<long long>(W) * H);
+        const int x = static_cast<int>(r % W) - 2, y = static_cast<int>(r / W) - 2;
+        if (x >= 0 && x < nx && y >= 0 && y < ny) continue;
+        const int xs = ((x % nx) + nx) % nx, ys = ((y % ny) + ny) % ny;
+        p[at<T>(I, a, x, y)] = p[at<T>(I, a, xs, ys)];
+    }
+}
+
+// f_a(z, t) = pop_a(z - e_a) + t_a rho_ref, for one plane a.
+template <typename T>
+__global__ void k_gather(const Inst* __restrict__ I, int parity, int a, double* __restrict__ out) {
+    const int nx = I->nx, ny = I->ny;
+    const long long N = static_cast<long long>(nx) * ny;
+    const T* p = popk<T>(I, parity);
+    const double off = tw(a) * static_cast<double>(phys<T>(I).rho_ref);
+    const int ex = cx(a), ey = cy(a);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % nx), y = static_cast<int>(i / nx);
+        out[i] = static_cast<double>(p[at<T>(I, a, x - ex, y - ey)]) + off;
+    }
+}
+
+// rho and momentum sum f e of node (x, y), x in [-1, nx], y in [-1, ny].
+template <typename T>
+__device__ __forceinline__ double node_rho(const Inst* I, const T* p, int x, int y, double* jx, double* jy) {
+    double r = 0.0, mx = 0.0, my = 0.0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const double v = static_cast<double>(p[at<T>(I, a, x - cx(a), y - cy(a))]);
+        r += v;
+        mx += cx(a) * v;
+        my += cy(a) * v;
+    }
+    if (jx) *jx = mx;
+    if (jy) *jy = my;
+    return r + static_cast<double>(phys<T>(I).rho_ref);
+}
+
+__device__ __forceinline__ double psi_of(const Phys<double>& P, double rho) {
+    return sqrt(psi_radicand(P, rho));
+}
+
+// rho, velocity (Eq. 9 force, rho u = sum f e + F/2) and psi of node (x, y).
+template <typename T>
+__device__ void node_fields(const Inst* I, const T* p, int x, int y, double* rho, double* ux, double* uy,
+                            double* psi) {
+    const Phys<double>& P = I->pd;
+    const int nx = I->nx, ny = I->ny;
+    double jx, jy;
+    const double r = node_rho<T>(I, p, x, y, &jx, &jy);
+    double Fx = 0.0, Fy = 0.0, ps = 0.0;
+    if (P.interact) {
+        ps = psi_of(P, r);
+        double gx1 = 0, gy1 = 0, gx2 = 0, gy2 = 0;
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            int xn = x + cx(a), yn = y + cy(a);
+            xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
+            yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
+            const double pn = psi_of(P, node_rho<T>(I, p, xn, yn, nullptr, nullptr));
+            const double w = (a < 5) ? 1.0 / 3.0 : 1.0 / 12.0;
+            gx1 += w * pn * cx(a);
+            gy1 += w * pn * cy(a);
+            gx2 += w * pn * pn * cx(a);
+            gy2 += w * pn * pn * cy(a);
+        }
+        Fx = -P.G * (0.5 * P.A * gx2 + (1.0 - P.A) * ps * gx1);
+        Fy = -P.G * (0.5 * P.A * gy2 + (1.0 - P.A) * ps * gy1);
+    }
+    *rho = r;
+    *ux = (jx + 0.5 * Fx) / r;
+    *uy = (jy + 0.5 * Fy) / r;
+    *psi = ps;
+}
+
+template <typename T>
+__global__ void k_field(const Inst* __restrict__ I, int parity, int field, double* __restrict__ out) {
+    const int nx = I->nx, ny = I->ny;
+    const long long N = static_cast<long long>(nx) * ny;
+    const T* p = popk<T>(I, parity);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % nx), y = static_cast<int>(i / nx);
+        double v;
+        if (field == 0) {
+            v = node_rho<T>(I, p, x, y, nullptr, nullptr);
+        } else if (field == 3) {
+            v = I->pd.interact ? psi_of(I->pd, node_rho<T>(I, p, x, y, nullptr, nullptr)) : 0.0;
+        } else {
+            double r, u, w, s;
+            node_fields<T>(I, p, x, y, &r, &u, &w, &s);
+            v = field == 1 ? u : w;
+        }
+        out[i] = v;
+    }
+}
+
+// ---- FP64 block reductions ----------------------------------------------
+// Each block writes kReduceSlots partial sums (slot `max_slot` is a max);
+// k_finish adds the partials in a fixed order, so results are deterministic.
+__device__ __forceinline__ void block_reduce_store(double (&v)[kReduceSlots], int max_slot, double* partials) {
+    __shared__ double red[kThreads / 32][kReduceSlots];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kReduceSlots; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            x = (k == max_slot) ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) red[warp][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kReduceSlots) {
+        const int k = threadIdx.x;
+        double x = red[0][k];
+        for (int w = 1; w < kThreads / 32; ++w) x = (k == max_slot) ? fmax(x, red[w][k]) : x + red[w][k];
+        partials[blockIdx.x * kReduceSlots + k] = x;
+    }
+}
+
+__global__ void k_finish(const double* __restrict__ partials, int nblocks, int max_slot, double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= kReduceSlots) return;
+    double x = partials[k];
+    for (int b = 1; b < nblocks; ++b) {
+        const double y = partials[b * kReduceSlots + k];
+        x = (k == max_slot) ? fmax(x, y) : x + y;
+    }
+    out[k] = x;
+}
+
+// Sums for Laplace's law: {sum rho, sum p_in, sum rho_in, n_in, sum p_out,
+// sum rho_out, n_out, 0}; p = p_EOS(rho) (equal to rho/3 + G psi^2/2, Eq. 10).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_measure(const Inst* __restrict__ I, int parity, double cxc, double cyc,
+                                                       double r_in, double r_out, double* __restrict__ partials) {
+    const int nx = I->nx, ny = I->ny;
+    const long long N = static_cast<long long>(nx) * ny;
+    const T* p = popk<T>(I, parity);
+    double v[kReduceSlots] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % nx), y = static_cast<int>(i / nx);
+        const double r = node_rho<T>(I, p, x, y, nullptr, nullptr);
+        double dx = x - cxc, dy = y - cyc;
+        dx -= nx * rint(dx / nx);
+        dy -= ny * rint(dy / ny);
+        const double d = sqrt(dx * dx + dy * dy);
+        v[0] += r;
+        if (d <= r_in) {
+            v[1] += p_eos(I->pd, r);
+            v[2] += r;
+            v[3] += 1.0;
+        }
+        if (d >= r_out) {
+            v[4] += p_eos(I->pd, r);
+            v[5] += r;
+            v[6] += 1.0;
+        }
+    }
+    block_reduce_store(v, -1, partials);
+}
+
+// {mass, sum rho u_x, sum rho u_y, sum rho |u|^2 / 2, max |u|, 0, 0, 0}
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_stats(const Inst* __restrict__ I, int parity, double* __restrict__ partials) {
+    const int nx = I->nx, ny = I->ny;
+    const long long N = static_cast<long long>(nx) * ny;
+    const T* p = popk<T>(I, parity);
+    double v[kReduceSlots] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % nx), y = static_cast<int>(i / nx);
+        double r, u, w, s;
+        node_fields<T>(I, p, x, y, &r, &u, &w, &s);
+        v[0] += r;
+        v[1] += r * u;
+        v[2] += r * w;
+        v[3] += 0.5 * r * (u * u + w * w);
+        v[4] = fmax(v[4], sqrt(u * u + w * w));
+    }
+    block_reduce_store(v, 4, partials);
+}
+
+int grid_for(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    if (b > 8 * kReduceBlocks) b = 8 * kReduceBlocks;
+    return static_cast<int>(b);
+}
+
+}  // namespace
+
+cudaError_t aux_init(const Inst& h, const Inst* d, const double* rho, const double* ux, const double* uy,
+                     int parity, cudaStream_t st) {
+    const long long N = static_cast<long long>(h.nx) * h.ny;
+    if (h.prec == LBM_FP32)
+        k_init<float><<<grid_for(N), kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    else
+        k_init<double><<<grid_for(N), kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return aux_fill_ghosts(h, d, parity, st);
+}
+
+cudaError_t aux_fill_ghosts(const Inst& h, const Inst* d, int parity, cudaStream_t st) {
+    const long long M = static_cast<long long>(h.nx + 4) * (h.ny + 4) * 9;
+    if (h.prec == LBM_FP32)
+        k_ghosts<float><<<grid_for(M), kThreads, 0, st>>>(d, parity);
+    else
+        k_ghosts<double><<<grid_for(M), kThreads, 0, st>>>(d, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_gather_plane(const Inst& h, const Inst* d, int parity, int a, double* out, cudaStream_t st) {
+    const long long N = static_cast<long long>(h.nx) * h.ny;
+    if (h.prec == LBM_FP32)
+        k_gather<float><<<grid_for(N), kThreads, 0, st>>>(d, parity, a, out);
+    else
+        k_gather<double><<<grid_for(N), kThreads, 0, st>>>(d, parity, a, out);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_field(const Inst& h, const Inst* d, int parity, int field, double* out, cudaStream_t st) {
+    const long long N = static_cast<long long>(h.nx) * h.ny;
+    if (h.prec == LBM_FP32)
+        k_field<float><<<grid_for(N), kThreads, 0, st>>>(d, parity, field, out);
+    else
+        k_field<double><<<grid_for(N), kThreads, 0, st>>>(d, parity, field, out);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_measure(const Inst& h, const Inst* d, int parity, double cxc, double cyc, double r_in,
+                        double r_out, double* partials, double* result, cudaStream_t st) {
+    if (h.prec == LBM_FP32)
+        k_measure<float><<<kReduceBlocks, kThreads, 0, st>>>(d, parity, cxc, cyc, r_in, r_out, partials);
+    else
+        k_measure<double><<<kReduceBlocks, kThreads, 0, st>>>(d, parity, cxc, cyc, r_in, r_out, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_finish<<<1, 32, 0, st>>>(partials, kReduceBlocks, -1, result);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_stats(const Inst& h, const Inst* d, int parity, double* partials, double* result, cudaStream_t st) {
+    if (h.prec == LBM_FP32)
+        k_stats<float><<<kReduceBlocks, kThreads, 0, st>>>(d, parity, partials);
+    else
+        k_stats<double><<<kReduceBlocks, kThreads, 0, st>>>(d, parity, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_finish<<<1, 32, 0, st>>>(partials, kReduceBlocks, 4, result);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

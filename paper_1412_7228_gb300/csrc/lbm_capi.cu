@@ -1,0 +1,995 @@
+// lbm_capi.cu -- the C ABI of include/lbm.h: contexts, device memory layout,
+// TMA tensor maps, parameters, launches (optionally from CUDA graphs),
+// read-back, checkpoints, the tile/schedule autotuner and the host-side EOS
+// helpers (critical point, Maxwell coexistence, Laplace fit).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using lbm::Inst;
+
+namespace {
+
+constexpr unsigned long long kTimeoutNs = 1000000000ull;   // bounded TMA wait: 1 s
+constexpr int kGraphSteps = 32;                            // steps per captured graph (even)
+
+struct HostParams {
+    lbm_eos eos;
+    double A, kappa, G, s[9], rho_ref;
+    unsigned flags;
+    int set;
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int esize(int prec) { return prec == LBM_FP32 ? 4 : (prec == LBM_FP64 ? 8 : 0); }
+int ghost_x(int prec) { return prec == LBM_FP32 ? lbm::Prec<float>::GX : lbm::Prec<double>::GX; }
+
+int pitch_of(int nx, int prec) {
+    const int per32 = 32 / esize(prec);
+    return static_cast<int>(align_up(static_cast<size_t>(ghost_x(prec) + nx + 2), per32));
+}
+
+struct Layout {
+    std::vector<size_t> pop_off[2];
+    size_t inst_off, tiles_off, status_off, partials_off, result_off, scratch_off, total;
+    size_t tiles_cap, scratch_elems;
+};
+
+bool valid_shape(int n, const int* nx, const int* ny, int prec) {
+    if (n < 1 || !nx || !ny || esize(prec) == 0) return false;
+    for (int i = 0; i < n; ++i)
+        if (nx[i] < 2 || ny[i] < 2 || nx[i] > (1 << 20) || ny[i] > (1 << 20)) return false;
+    return true;
+}
+
+Layout make_layout(int n, const int* nx, const int* ny, int prec) {
+    Layout L;
+    size_t off = 0;
+    const size_t es = esize(prec);
+    size_t maxN = 0, tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t plane = static_cast<size_t>(pitch_of(nx[i], prec)) * (ny[i] + 2 * lbm::GY);
+        for (int k = 0; k < 2; ++k) {
+            L.pop_off[k].push_back(off);
+            off = align_up(off + 9 * plane * es, 256);
+        }
+        maxN = std::max(maxN, static_cast<size_t>(nx[i]) * ny[i]);
+    }
+    for (int c = 0; c < lbm::step_config_count(prec); ++c) {
+        const lbm::TileCfg t = lbm::step_config(prec, c);
+        size_t s = 0;
+        for (int i = 0; i < n; ++i) s += static_cast<size_t>((nx[i] + t.bx - 1) / t.bx) * ((ny[i] + t.by - 1) / t.by);
+        tiles = std::max(tiles, s);
+    }
+    L.inst_off = off;
+    off = align_up(off + n * sizeof(Inst), 256);
+    L.tiles_off = off;
+    L.tiles_cap = tiles;
+    off = align_up(off + tiles * sizeof(int4), 256);
+    L.status_off = off;
+    off = align_up(off + n * sizeof(int), 256);
+    L.partials_off = off;
+    off = align_up(off + lbm::kReduceBlocks * lbm::kReduceSlots * sizeof(double), 256);
+    L.result_off = off;
+    off = align_up(off + lbm::kReduceSlots * sizeof(double), 256);
+    L.scratch_off = off;
+    L.scratch_elems = 3 * maxN;
+    off = align_up(off + L.scratch_elems * sizeof(double), 256);
+    L.total = off;
+    return L;
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled get_encoder() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// ---- host EOS (independent numerical routines) ---------------------------
+double eos_p(const lbm_eos& e, double rho) {
+    const double RT = e.R * e.T;
+    if (e.kind == LBM_EOS_CS) {
+        const double n = e.b * rho / 4.0, q = 1.0 - n;
+        return e.K * (rho * RT * (1.0 + n + n * n - n * n * n) / (q * q * q) - e.a * rho * rho);
+    }
+    if (e.kind == LBM_EOS_VDW) return e.K * (rho * RT / (1.0 - e.b * rho) - e.a * rho * rho);
+    const double m = 0.37464 + 1.54226 * e.omega - 0.26992 * e.omega * e.omega;
+    const double sq = 1.0 + m * (1.0 - std::sqrt(e.T / e.Tc));
+    const double br = e.b * rho;
+    return e.K * (rho * RT / (1.0 - br) - e.a * sq * sq * rho * rho / (1.0 + 2.0 * br - br * br));
+}
+
+double eos_dp(const lbm_eos& e, double rho) {
+    const double RT = e.R * e.T;
+    if (e.kind == LBM_EOS_CS) {
+        const double n = e.b * rho / 4.0, q = 1.0 - n;
+        return e.K * (RT * (1.0 + 4.0 * n + 4.0 * n * n - 4.0 * n * n * n + n * n * n * n) / (q * q * q * q) -
+                      2.0 * e.a * rho);
+    }
+    if (e.kind == LBM_EOS_VDW) {
+        const double q = 1.0 - e.b * rho;
+        return e.K * (RT / (q * q) - 2.0 * e.a * rho);
+    }
+    const double m = 0.37464 + 1.54226 * e.omega - 0.26992 * e.omega * e.omega;
+    const double sq = 1.0 + m * (1.0 - std::sqrt(e.T / e.Tc));
+    const double br = e.b * rho, D = 1.0 + 2.0 * br - br * br, q = 1.0 - br;
+    return e.K * (RT / (q * q) - e.a * sq * sq * (2.0 * rho + 2.0 * e.b * rho * rho) / (D * D));
+}
+
+double eos_rho_max(const lbm_eos& e) { return e.kind == LBM_EOS_CS ? 4.0 / e.b : 1.0 / e.b; }
+
+bool eos_valid(const lbm_eos* e) {
+    if (!e || (e->kind != LBM_EOS_CS && e->kind != LBM_EOS_VDW && e->kind != LBM_EOS_PR)) return false;
+    if (!(e->a > 0) || !(e->b > 0) || !(e->R > 0) || !(e->K > 0) || !std::isfinite(e->a + e->b + e->R + e->K))
+        return false;
+    if (e->kind == LBM_EOS_PR && !(e->Tc > 0)) return false;
+    return true;
+}
+
+// argmin over (lo, hi) of a unimodal function, golden section
+template <class F> double golden_min(F f, double lo, double hi, double* fmin) {
+    const double g = 0.5 * (std::sqrt(5.0) - 1.0);
+    double a = lo, b = hi, c = b - g * (b - a), d = a + g * (b - a);
+    double fc = f(c), fd = f(d);
+    for (int it = 0; it < 300 && (b - a) > 1e-15 * (std::fabs(a) + std::fabs(b)); ++it) {
+        if (fc < fd) { b = d; d = c; fd = fc; c = b - g * (b - a); fc = f(c); }
+        else { a = c; c = d; fc = fd; d = a + g * (b - a); fd = f(d); }
+    }
+    const double x = 0.5 * (a + b);
+    *fmin = f(x);
+    return x;
+}
+
+template <class F> double bisect(F f, double lo, double hi) {
+    double flo = f(lo);
+    for (int it = 0; it < 400; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double fm = f(mid);
+        if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+    }
+    return 0.5 * (lo + hi);
+}
+
+// composite 8-point Gauss-Legendre
+double gauss_int(const lbm_eos& e, double p0, double a, double b, int panels) {
+    static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    static const double wg[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    double s = 0.0;
+    const double h = (b - a) / panels;
+    for (int k = 0; k < panels; ++k) {
+        const double c = a + (k + 0.5) * h, r = 0.5 * h;
+        for (int j = 0; j < 4; ++j)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const double x = c + sg * r * xg[j];
+                s += wg[j] * r * (p0 - eos_p(e, x)) / (x * x);
+            }
+    }
+    return s;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    int n = 0, prec = 0, esz = 0, device = 0;
+    std::vector<int> nx, ny;
+    std::vector<Inst> h;
+    std::vector<HostParams> hp;
+    std::vector<int> inited;
+    Layout L;
+    char* buf = nullptr;
+    size_t buf_bytes = 0;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    Inst* d_inst = nullptr;
+    int4* d_tiles = nullptr;
+    int ntiles = 0;
+    int* d_status = nullptr;
+    double* d_partials = nullptr;
+    double* d_result = nullptr;
+    double* d_scratch = nullptr;
+    int parity = 0;
+    long long steps = 0, launches = 0;
+    int cfg = 0, sched = 0;
+    bool use_graphs = false;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const char* fmt, const char* detail = "") {
+    if (c) {
+        char b[512];
+        std::snprintf(b, sizeof b, fmt, detail);
+        c->err = b;
+    }
+    return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return LBM_ECUDA;
+}
+
+#define CK(c, call)                                            \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+    } while (0)
+
+void drop_graphs(lbm_ctx* c) {
+    for (auto& g : c->gexec)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+int encode_maps(lbm_ctx* c) {
+    EncodeTiled enc = get_encoder();
+    if (!enc) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver%s");
+    const lbm::TileCfg t = lbm::step_config(c->prec, c->cfg);
+    const int HX = c->prec == LBM_FP32 ? lbm::Prec<float>::HX : lbm::Prec<double>::HX;
+    for (int i = 0; i < c->n; ++i) {
+        Inst& I = c->h[i];
+        for (int k = 0; k < 2; ++k) {
+            cuuint64_t dims[3] = {static_cast<cuuint64_t>(I.pitch), static_cast<cuuint64_t>(I.nyp), 9};
+            cuuint64_t strides[2] = {static_cast<cuuint64_t>(I.pitch) * c->esz,
+                                     static_cast<cuuint64_t>(I.plane) * c->esz};
+            cuuint32_t box[3] = {static_cast<cuuint32_t>(t.bx + 2 * HX), static_cast<cuuint32_t>(t.by + 2 * lbm::GY), 9};
+            cuuint32_t es[3] = {1, 1, 1};
+            CUresult r = enc(&I.tmap[k], c->prec == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                             3, I.pop[k], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                char msg[64];
+                std::snprintf(msg, sizeof msg, "%d", static_cast<int>(r));
+                return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed with CUresult %s", msg);
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+int upload_insts(lbm_ctx* c) {
+    CK(c, cudaMemcpyAsync(c->d_inst, c->h.data(), c->n * sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int build_tiles(lbm_ctx* c) {
+    const lbm::TileCfg t = lbm::step_config(c->prec, c->cfg);
+    std::vector<std::vector<int4>> per(c->n);
+    for (int i = 0; i < c->n; ++i) {
+        const int tx = (c->nx[i] + t.bx - 1) / t.bx, ty = (c->ny[i] + t.by - 1) / t.by;
+        for (int y = 0; y < ty; ++y)
+            for (int x = 0; x < tx; ++x) per[i].push_back(make_int4(i, x * t.bx, y * t.by, 0));
+    }
+    std::vector<int> order(c->n);
+    for (int i = 0; i < c->n; ++i) order[i] = i;
+    std::vector<int4> all;
+    if (c->sched == 1) {
+        size_t most = 0;
+        for (auto& v : per) most = std::max(most, v.size());
+        for (size_t k = 0; k < most; ++k)
+            for (int i = 0; i < c->n; ++i)
+                if (k < per[i].size()) all.push_back(per[i][k]);
+    } else {
+        if (c->sched == 2)
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
+        for (int i : order) all.insert(all.end(), per[i].begin(), per[i].end());
+    }
+    if (all.size() > c->L.tiles_cap) return fail(c, LBM_ENOMEM, "tile table larger than reserved%s");
+    c->ntiles = static_cast<int>(all.size());
+    CK(c, cudaMemcpyAsync(c->d_tiles, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int apply_schedule(lbm_ctx* c, int cfg, int sched) {
+    c->cfg = cfg;
+    c->sched = sched;
+    drop_graphs(c);
+    CK(c, lbm::step_prepare(c->prec, cfg));
+    int rc = encode_maps(c);
+    if (rc) return rc;
+    rc = upload_insts(c);
+    if (rc) return rc;
+    return build_tiles(c);
+}
+
+template <typename T> void fill_phys(lbm::Phys<T>& P, const HostParams& hp) {
+    const lbm_eos& e = hp.eos;
+    P.eos = e.kind;
+    P.flags = hp.flags;
+    P.K = T(e.K);
+    P.a = T(e.a);
+    P.b = T(e.b);
+    P.b4 = T(e.b / 4.0);
+    P.RT = T(e.R * e.T);
+    double aal = e.a;
+    if (e.kind == LBM_EOS_PR) {
+        const double m = 0.37464 + 1.54226 * e.omega - 0.26992 * e.omega * e.omega;
+        const double sq = 1.0 + m * (1.0 - std::sqrt(e.T / e.Tc));
+        aal = e.a * sq * sq;
+    }
+    P.aalpha = T(aal);
+    P.A = T(hp.A);
+    P.kappa = T(hp.kappa);
+    P.G = T(hp.G);
+    P.two_over_G = hp.G != 0.0 ? T(2.0 / hp.G) : T(0);
+    P.interact = hp.G != 0.0;
+    for (int k = 0; k < 9; ++k) {
+        P.s[k] = T(hp.s[k]);
+        P.hs[k] = T(1.0 - 0.5 * hp.s[k]);
+    }
+    P.c1 = T(1.5 * hp.s[1]);
+    P.c2 = (hp.flags & LBM_FLAG_LI_EPS) ? T(-1.5 * hp.s[2]) : T(0);
+    P.rho_ref = T(hp.rho_ref);
+}
+
+int check_idx(lbm_ctx* c, int i) {
+    if (!c) return LBM_EINVAL;
+    if (i < 0 || i >= c->n) return fail(c, LBM_EINVAL, "instance index out of range%s");
+    return LBM_OK;
+}
+
+int status_of(lbm_ctx* c, int i, int* code) {
+    int st = 0;
+    CK(c, cudaMemcpy(&st, c->d_status + i, sizeof(int), cudaMemcpyDeviceToHost));
+    *code = (st & lbm::ST_UNSTABLE) ? LBM_EUNSTABLE : ((st & lbm::ST_TIMEOUT) ? LBM_ETIMEOUT : LBM_OK);
+    return LBM_OK;
+}
+
+int sync_all(lbm_ctx* c) {
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::vector<int> st(c->n);
+    CK(c, cudaMemcpy(st.data(), c->d_status, c->n * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < c->n; ++i) {
+        if (st[i] & lbm::ST_UNSTABLE) {
+            char m[32];
+            std::snprintf(m, sizeof m, "%d", i);
+            return fail(c, LBM_EUNSTABLE, "instance %s: a density left the psi domain of the EOS or became NaN", m);
+        }
+        if (st[i] & lbm::ST_TIMEOUT) {
+            char m[32];
+            std::snprintf(m, sizeof m, "%d", i);
+            return fail(c, LBM_ETIMEOUT, "instance %s: a bounded device wait gave up", m);
+        }
+    }
+    return LBM_OK;
+}
+
+int launch_steps(lbm_ctx* c, int n) {
+    for (int k = 0; k < n; ++k) {
+        CK(c, lbm::step_launch(c->prec, c->cfg, c->d_inst, c->d_tiles, c->ntiles, c->parity, kTimeoutNs, c->stream));
+        c->parity ^= 1;
+        ++c->launches;
+        ++c->steps;
+    }
+    return LBM_OK;
+}
+
+int ensure_graph(lbm_ctx* c, int parity) {
+    if (c->gexec[parity]) return LBM_OK;
+    cudaGraph_t g;
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < kGraphSteps; ++k) {
+        cudaError_t e = lbm::step_launch(c->prec, c->cfg, c->d_inst, c->d_tiles, c->ntiles, parity ^ (k & 1),
+                                         kTimeoutNs, c->stream);
+        if (e != cudaSuccess) {
+            cudaStreamEndCapture(c->stream, &g);
+            return cuda_fail(c, e, "step launch during graph capture");
+        }
+    }
+    CK(c, cudaStreamEndCapture(c->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&c->gexec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    return LBM_OK;
+}
+
+int ready(lbm_ctx* c) {
+    for (int i = 0; i < c->n; ++i) {
+        if (!c->hp[i].set) return fail(c, LBM_EINVAL, "parameters of an instance were never set%s");
+        if (!c->inited[i]) return fail(c, LBM_EINVAL, "an instance was never initialised%s");
+    }
+    return LBM_OK;
+}
+
+int valid_params(const lbm_eos* eos, double A, double kappa, double G, const double* s, double rho_ref) {
+    if (!eos_valid(eos) || !s) return 0;
+    if (!std::isfinite(A) || !std::isfinite(kappa) || !std::isfinite(G) || !std::isfinite(rho_ref)) return 0;
+    if (!(eos->T > 0) || !std::isfinite(eos->T)) return 0;
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(s[k]) || s[k] <= 0.0 || s[k] >= 2.0) return 0;
+    return 1;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+int lbm_eos_pressure(const lbm_eos* eos, double rho, double* p) {
+    if (!eos_valid(eos) || !p || !(rho >= 0)) return LBM_EINVAL;
+    *p = eos_p(*eos, rho);
+    return LBM_OK;
+}
+
+int lbm_eos_critical(const lbm_eos* eos, double* rho_c, double* T_c, double* p_c) {
+    if (!eos_valid(eos)) return LBM_EINVAL;
+    lbm_eos e = *eos;
+    const double hi = eos_rho_max(e);
+    auto min_slope = [&](double T, double* arg) {
+        e.T = T;
+        double fm;
+        *arg = golden_min([&](double r) { return eos_dp(e, r); }, 1e-9 * hi, 0.999 * hi, &fm);
+        return fm;
+    };
+    double lo = 1e-9, up = 1.0, arg;
+    for (int it = 0; it < 200 && min_slope(up, &arg) <= 0; ++it) up *= 2.0;
+    const double Tc = bisect([&](double T) { double a2; return min_slope(T, &a2); }, lo, up);
+    min_slope(Tc, &arg);
+    e.T = Tc;
+    if (rho_c) *rho_c = arg;
+    if (T_c) *T_c = Tc;
+    if (p_c) *p_c = eos_p(e, arg);
+    return LBM_OK;
+}
+
+int lbm_eos_maxwell(const lbm_eos* eos, double* rho_g, double* rho_l, double* p0_out) {
+    if (!eos_valid(eos) || !(eos->T > 0)) return LBM_EINVAL;
+    const lbm_eos& e = *eos;
+    const double hi = eos_rho_max(e);
+    double fm;
+    const double rm = golden_min([&](double r) { return eos_dp(e, r); }, 1e-9 * hi, 0.999 * hi, &fm);
+    if (!(fm < 0)) return LBM_EINVAL;   // not below the critical temperature
+    const double s1 = bisect([&](double r) { return eos_dp(e, r); }, 1e-12 * hi, rm);
+    const double s2 = bisect([&](double r) { return -eos_dp(e, r); }, rm, 0.99999 * hi);
+    const double p_hi = eos_p(e, s1), p_lo = std::max(eos_p(e, s2), 0.0);
+    auto roots = [&](double p0, double* rg, double* rl) {
+        *rg = bisect([&](double r) { return eos_p(e, r) - p0; }, 0.0, s1);
+        *rl = bisect([&](double r) { return eos_p(e, r) - p0; }, s2, 0.99999999 * hi);
+    };
+    auto area = [&](double p0) {
+        double rg, rl;
+        roots(p0, &rg, &rl);
+        return gauss_int(e, p0, rg, s1, 256) + gauss_int(e, p0, s1, s2, 256) + gauss_int(e, p0, s2, rl, 256);
+    };
+    const double span = p_hi - p_lo;
+    double a = p_lo + 1e-12 * span, b = p_hi - 1e-12 * span;
+    double fa = area(a);
+    if (!((fa < 0) != (area(b) < 0))) return LBM_EINVAL;
+    for (int it = 0; it < 200; ++it) {
+        const double m = 0.5 * (a + b);
+        if (m <= a || m >= b) break;
+        const double fmid = area(m);
+        if ((fmid < 0) == (fa < 0)) { a = m; fa = fmid; } else { b = m; }
+    }
+    const double p0 = 0.5 * (a + b);
+    double rg, rl;
+    roots(p0, &rg, &rl);
+    if (rho_g) *rho_g = rg;
+    if (rho_l) *rho_l = rl;
+    if (p0_out) *p0_out = p0;
+    return LBM_OK;
+}
+
+int lbm_laplace_fit(int n, const double* dp, const double* R, double* sigma, double* icpt, double* r2) {
+    if (n < 2 || !dp || !R) return LBM_EINVAL;
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!(R[i] > 0)) return LBM_EINVAL;
+        const double x = 1.0 / R[i];
+        sx += x; sy += dp[i]; sxx += x * x; sxy += x * dp[i];
+    }
+    const double den = n * sxx - sx * sx;
+    if (den == 0.0) return LBM_EINVAL;
+    const double k = (n * sxy - sx * sy) / den, c = (sy - k * sx) / n;
+    double ssr = 0, sst = 0;
+    const double ym = sy / n;
+    for (int i = 0; i < n; ++i) {
+        const double y = k / R[i] + c;
+        ssr += (dp[i] - y) * (dp[i] - y);
+        sst += (dp[i] - ym) * (dp[i] - ym);
+    }
+    if (sigma) *sigma = k;
+    if (icpt) *icpt = c;
+    if (r2) *r2 = sst > 0 ? 1.0 - ssr / sst : 1.0;
+    return LBM_OK;
+}
+
+size_t lbm_batch_required_bytes(int n, const int* nx, const int* ny, int precision) {
+    if (!valid_shape(n, nx, ny, precision)) return 0;
+    return make_layout(n, nx, ny, precision).total;
+}
+
+size_t lbm_required_bytes(int nx, int ny, int precision) { return lbm_batch_required_bytes(1, &nx, &ny, precision); }
+
+int lbm_batch_create(lbm_ctx** out, int n, const int* nx, const int* ny, int precision, void* dev_buf,
+                     size_t buf_bytes, void* stream) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (!valid_shape(n, nx, ny, precision)) return LBM_EINVAL;
+    if (dev_buf && (reinterpret_cast<uintptr_t>(dev_buf) % 256) != 0) return LBM_EINVAL;
+    lbm_ctx* c = new lbm_ctx();
+    c->n = n;
+    c->prec = precision;
+    c->esz = esize(precision);
+    c->nx.assign(nx, nx + n);
+    c->ny.assign(ny, ny + n);
+    c->L = make_layout(n, nx, ny, precision);
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->hp.assign(n, HostParams{});
+    c->inited.assign(n, 0);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return LBM_ECUDA;
+    }
+    if (dev_buf) {
+        if (buf_bytes < c->L.total) {
+            delete c;
+            return LBM_ENOMEM;
+        }
+        c->buf = static_cast<char*>(dev_buf);
+        c->buf_bytes = buf_bytes;
+    } else {
+        if (cudaMalloc(&c->buf, c->L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return LBM_ENOMEM;
+        }
+        c->owns = true;
+        c->buf_bytes = c->L.total;
+    }
+    if (cudaMemsetAsync(c->buf, 0, c->L.total, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        lbm_destroy(c);
+        return LBM_ECUDA;
+    }
+    c->d_inst = reinterpret_cast<Inst*>(c->buf + c->L.inst_off);
+    c->d_tiles = reinterpret_cast<int4*>(c->buf + c->L.tiles_off);
+    c->d_status = reinterpret_cast<int*>(c->buf + c->L.status_off);
+    c->d_partials = reinterpret_cast<double*>(c->buf + c->L.partials_off);
+    c->d_result = reinterpret_cast<double*>(c->buf + c->L.result_off);
+    c->d_scratch = reinterpret_cast<double*>(c->buf + c->L.scratch_off);
+    c->h.assign(n, Inst{});
+    for (int i = 0; i < n; ++i) {
+        Inst& I = c->h[i];
+        std::memset(&I, 0, sizeof(Inst));
+        I.pop[0] = c->buf + c->L.pop_off[0][i];
+        I.pop[1] = c->buf + c->L.pop_off[1][i];
+        I.status = c->d_status + i;
+        I.nx = nx[i];
+        I.ny = ny[i];
+        I.pitch = pitch_of(nx[i], precision);
+        I.nyp = ny[i] + 2 * lbm::GY;
+        I.plane = static_cast<long long>(I.pitch) * I.nyp;
+        I.prec = precision;
+    }
+    int rc = apply_schedule(c, 0, 0);
+    if (rc) {
+        lbm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_create(lbm_ctx** out, int nx, int ny, int precision, void* dev_buf, size_t buf_bytes, void* stream) {
+    return lbm_batch_create(out, 1, &nx, &ny, precision, dev_buf, buf_bytes, stream);
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream || c->buf) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->owns && c->buf) cudaFree(c->buf);
+    delete c;
+}
+
+int lbm_batch_set_params(lbm_ctx* c, int i, const lbm_eos* eos, double A, double kappa, double G, const double s[9],
+                         double rho_ref, unsigned flags) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!valid_params(eos, A, kappa, G, s, rho_ref)) return fail(c, LBM_EINVAL, "invalid model parameters%s");
+    CK(c, cudaSetDevice(c->device));
+    HostParams& hp = c->hp[i];
+    hp.eos = *eos;
+    hp.A = A;
+    hp.kappa = kappa;
+    hp.G = G;
+    std::memcpy(hp.s, s, sizeof hp.s);
+    hp.rho_ref = rho_ref;
+    hp.flags = flags;
+    hp.set = 1;
+    fill_phys(c->h[i].pf, hp);
+    fill_phys(c->h[i].pd, hp);
+    drop_graphs(c);
+    return upload_insts(c);
+}
+
+int lbm_set_params(lbm_ctx* c, const lbm_eos* eos, double A, double kappa, double G, const double s[9], double rho_ref,
+                   unsigned flags) {
+    return lbm_batch_set_params(c, 0, eos, A, kappa, G, s, rho_ref, flags);
+}
+
+int lbm_batch_init_density(lbm_ctx* c, int i, const double* rho, const double* ux, const double* uy) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!rho) return fail(c, LBM_EINVAL, "rho must not be NULL%s");
+    if (!c->hp[i].set) return fail(c, LBM_EINVAL, "set the parameters before the density%s");
+    const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
+    // the EOS range only matters when psi is evaluated (G != 0)
+    const double rmax = c->hp[i].G != 0.0 ? eos_rho_max(c->hp[i].eos) : HUGE_VAL;
+    for (size_t k = 0; k < N; ++k) {
+        if (!(rho[k] > 0.0) || !(rho[k] < rmax) || !std::isfinite(rho[k]))
+            return fail(c, LBM_EINVAL, "initial density must be finite, positive and inside the EOS range%s");
+        if ((ux && !std::isfinite(ux[k])) || (uy && !std::isfinite(uy[k])))
+            return fail(c, LBM_EINVAL, "initial velocity must be finite%s");
+    }
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaStreamSynchronize(c->stream));
+    double* d_rho = c->d_scratch;
+    double* d_ux = ux ? c->d_scratch + N : nullptr;
+    double* d_uy = uy ? c->d_scratch + 2 * N : nullptr;
+    CK(c, cudaMemcpyAsync(d_rho, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (ux) CK(c, cudaMemcpyAsync(d_ux, ux, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (uy) CK(c, cudaMemcpyAsync(d_uy, uy, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, lbm::aux_init(c->h[i], c->d_inst + i, d_rho, d_ux, d_uy, c->parity, c->stream));
+    CK(c, cudaMemsetAsync(c->d_status + i, 0, sizeof(int), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->inited[i] = 1;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_init_density(lbm_ctx* c, const double* rho, const double* ux, const double* uy) {
+    return lbm_batch_init_density(c, 0, rho, ux, uy);
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+    if (!c || n < 0) return LBM_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    CK(c, cudaSetDevice(c->device));
+    if (c->use_graphs && n >= kGraphSteps) {
+        while (n >= kGraphSteps) {
+            rc = ensure_graph(c, c->parity);
+            if (rc) return rc;
+            CK(c, cudaGraphLaunch(c->gexec[c->parity], c->stream));
+            c->launches += kGraphSteps;
+            c->steps += kGraphSteps;
+            n -= kGraphSteps;   // an even number of steps: parity is unchanged
+        }
+    }
+    return launch_steps(c, n);
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    return sync_all(c);
+}
+
+int lbm_status(lbm_ctx* c, int i) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaStreamSynchronize(c->stream));
+    int code = LBM_OK;
+    rc = status_of(c, i, &code);
+    return rc ? rc : code;
+}
+
+int lbm_clear_status(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaMemsetAsync(c->d_status, 0, c->n * sizeof(int), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_batch_read_fields(lbm_ctx* c, int i, double* rho, double* ux, double* uy, double* psi) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
+    CK(c, cudaSetDevice(c->device));
+    const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
+    double* outs[4] = {rho, ux, uy, psi};
+    for (int f = 0; f < 4; ++f) {
+        if (!outs[f]) continue;
+        CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, c->d_scratch, c->stream));
+        CK(c, cudaMemcpyAsync(outs[f], c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    int code = LBM_OK;
+    rc = status_of(c, i, &code);
+    return rc ? rc : code;
+}
+
+int lbm_read_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* psi) {
+    return lbm_batch_read_fields(c, 0, rho, ux, uy, psi);
+}
+
+int lbm_batch_read_populations(lbm_ctx* c, int i, double* f) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!f) return fail(c, LBM_EINVAL, "f must not be NULL%s");
+    if (!c->inited[i]) return fail(c, LBM_EINVAL, "instance not initialised%s");
+    CK(c, cudaSetDevice(c->device));
+    const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
+    for (int a = 0; a < 9; ++a) {
+        CK(c, lbm::aux_gather_plane(c->h[i], c->d_inst + i, c->parity, a, c->d_scratch, c->stream));
+        CK(c, cudaMemcpyAsync(f + a * N, c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    int code = LBM_OK;
+    rc = status_of(c, i, &code);
+    return rc ? rc : code;
+}
+
+int lbm_read_populations(lbm_ctx* c, double* f) { return lbm_batch_read_populations(c, 0, f); }
+
+int lbm_batch_measure(lbm_ctx* c, int i, double cxc, double cyc, double r_in, double r_out, double* out) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!out || !(r_in >= 0) || !(r_out >= 0)) return fail(c, LBM_EINVAL, "bad measurement arguments%s");
+    if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
+    CK(c, cudaSetDevice(c->device));
+    CK(c, lbm::aux_measure(c->h[i], c->d_inst + i, c->parity, cxc, cyc, r_in, r_out, c->d_partials, c->d_result,
+                           c->stream));
+    double s[lbm::kReduceSlots];
+    CK(c, cudaMemcpyAsync(s, c->d_result, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double N = static_cast<double>(c->nx[i]) * c->ny[i];
+    const double p_in = s[3] > 0 ? s[1] / s[3] : NAN, rho_in = s[3] > 0 ? s[2] / s[3] : NAN;
+    const double p_out = s[6] > 0 ? s[4] / s[6] : NAN, rho_out = s[6] > 0 ? s[5] / s[6] : NAN;
+    const double ex = s[0] - rho_out * N;
+    const double R_eq = std::sqrt(std::max(ex, 0.0) / (M_PI * (rho_in - rho_out)));
+    const double vals[LBM_MEASURE_N] = {p_in, p_out, rho_in, rho_out, R_eq, s[0], s[3], s[6]};
+    std::memcpy(out, vals, sizeof vals);
+    int code = LBM_OK;
+    rc = status_of(c, i, &code);
+    return rc ? rc : code;
+}
+
+int lbm_measure_pressure_jump(lbm_ctx* c, double cxc, double cyc, double r_in, double r_out, double* p_in,
+                              double* p_out, double* R_eq) {
+    double o[LBM_MEASURE_N];
+    int rc = lbm_batch_measure(c, 0, cxc, cyc, r_in, r_out, o);
+    if (rc == LBM_OK || rc == LBM_EUNSTABLE || rc == LBM_ETIMEOUT) {
+        if (p_in) *p_in = o[0];
+        if (p_out) *p_out = o[1];
+        if (R_eq) *R_eq = o[4];
+    }
+    return rc;
+}
+
+int lbm_batch_stats(lbm_ctx* c, int i, double* out5) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!out5) return fail(c, LBM_EINVAL, "out must not be NULL%s");
+    if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
+    CK(c, cudaSetDevice(c->device));
+    CK(c, lbm::aux_stats(c->h[i], c->d_inst + i, c->parity, c->d_partials, c->d_result, c->stream));
+    double s[lbm::kReduceSlots];
+    CK(c, cudaMemcpyAsync(s, c->d_result, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::memcpy(out5, s, 5 * sizeof(double));
+    int code = LBM_OK;
+    rc = status_of(c, i, &code);
+    return rc ? rc : code;
+}
+
+int lbm_stats(lbm_ctx* c, double* mass, double* mom_x, double* mom_y, double* ke, double* umax) {
+    double o[5];
+    int rc = lbm_batch_stats(c, 0, o);
+    if (rc == LBM_OK || rc == LBM_EUNSTABLE || rc == LBM_ETIMEOUT) {
+        if (mass) *mass = o[0];
+        if (mom_x) *mom_x = o[1];
+        if (mom_y) *mom_y = o[2];
+        if (ke) *ke = o[3];
+        if (umax) *umax = o[4];
+    }
+    return rc;
+}
+
+// ---- checkpoints ----------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int version, n, prec, pad;
+    long long steps;
+};
+}  // namespace
+
+int lbm_save(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    rc = sync_all(c);
+    if (rc) return rc;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, LBM_EIO, "cannot open %s for writing", path);
+    CkptHeader hd{};
+    std::memcpy(hd.magic, "LBMCKPT1", 8);
+    hd.version = 1;
+    hd.n = c->n;
+    hd.prec = c->prec;
+    hd.steps = c->steps;
+    bool ok = std::fwrite(&hd, sizeof hd, 1, fp) == 1;
+    for (int i = 0; i < c->n && ok; ++i) {
+        int dims[2] = {c->nx[i], c->ny[i]};
+        ok = std::fwrite(dims, sizeof dims, 1, fp) == 1 && std::fwrite(&c->hp[i], sizeof(HostParams), 1, fp) == 1;
+        const size_t bytes = 9 * static_cast<size_t>(c->h[i].plane) * c->esz;
+        std::vector<char> host(bytes);
+        if (cudaMemcpy(host.data(), c->h[i].pop[c->parity], bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(fp);
+            return fail(c, LBM_ECUDA, "device-to-host copy of the populations failed%s");
+        }
+        ok = ok && std::fwrite(host.data(), 1, bytes, fp) == bytes;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(c, LBM_EIO, "writing %s failed", path);
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_EINVAL;
+    CK(c, cudaSetDevice(c->device));
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, LBM_EIO, "cannot open %s", path);
+    CkptHeader hd{};
+    if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, "LBMCKPT1", 8) != 0 || hd.version != 1 ||
+        hd.n != c->n || hd.prec != c->prec) {
+        std::fclose(fp);
+        return fail(c, LBM_EIO, "%s is not a checkpoint of this context's shape and precision", path);
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->n; ++i) {
+        int dims[2];
+        HostParams hp;
+        if (std::fread(dims, sizeof dims, 1, fp) != 1 || dims[0] != c->nx[i] || dims[1] != c->ny[i] ||
+            std::fread(&hp, sizeof hp, 1, fp) != 1) {
+            std::fclose(fp);
+            return fail(c, LBM_EIO, "%s does not match this context", path);
+        }
+        const size_t bytes = 9 * static_cast<size_t>(c->h[i].plane) * c->esz;
+        std::vector<char> host(bytes);
+        if (std::fread(host.data(), 1, bytes, fp) != bytes) {
+            std::fclose(fp);
+            return fail(c, LBM_EIO, "%s is truncated", path);
+        }
+        c->hp[i] = hp;
+        fill_phys(c->h[i].pf, hp);
+        fill_phys(c->h[i].pd, hp);
+        if (cudaMemcpy(c->h[i].pop[c->parity], host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(fp);
+            return fail(c, LBM_ECUDA, "host-to-device copy of the populations failed%s");
+        }
+        c->inited[i] = 1;
+    }
+    std::fclose(fp);
+    c->steps = hd.steps;
+    drop_graphs(c);
+    CK(c, cudaMemset(c->d_status, 0, c->n * sizeof(int)));
+    return upload_insts(c);
+}
+
+// ---- tiles, schedules, autotuning ----------------------------------------
+int lbm_tile_config_count(int precision) {
+    if (esize(precision) == 0) return LBM_EINVAL;
+    return lbm::step_config_count(precision);
+}
+
+int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads) {
+    if (esize(precision) == 0 || k < 0 || k >= lbm::step_config_count(precision)) return LBM_EINVAL;
+    const lbm::TileCfg t = lbm::step_config(precision, k);
+    if (bx) *bx = t.bx;
+    if (by) *by = t.by;
+    if (threads) *threads = t.threads;
+    return LBM_OK;
+}
+
+int lbm_set_schedule(lbm_ctx* c, int tile_config, int schedule) {
+    if (!c) return LBM_EINVAL;
+    if (tile_config < 0 || tile_config >= lbm::step_config_count(c->prec) || schedule < 0 || schedule >= lbm::kMaxSched)
+        return fail(c, LBM_EINVAL, "unknown tile configuration or schedule%s");
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return apply_schedule(c, tile_config, schedule);
+}
+
+int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double* ms_per_step) {
+    if (!c || steps < 1) return LBM_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    rc = sync_all(c);
+    if (rc) return rc;
+    // snapshot every instance's current time level, the counters and the status
+    std::vector<std::vector<char>> snap(c->n);
+    for (int i = 0; i < c->n; ++i) {
+        const size_t bytes = 9 * static_cast<size_t>(c->h[i].plane) * c->esz;
+        snap[i].resize(bytes);
+        CK(c, cudaMemcpy(snap[i].data(), c->h[i].pop[c->parity], bytes, cudaMemcpyDeviceToHost));
+    }
+    const int parity0 = c->parity;
+    const long long steps0 = c->steps, launches0 = c->launches;
+    const bool graphs0 = c->use_graphs;
+    c->use_graphs = false;
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    double best = 1e300;
+    int bc = c->cfg, bs = c->sched;
+    const int nsched = c->n > 1 ? lbm::kMaxSched : 1;
+    for (int k = 0; k < lbm::step_config_count(c->prec); ++k)
+        for (int s = 0; s < nsched; ++s) {
+            rc = apply_schedule(c, k, s);
+            if (rc) break;
+            rc = launch_steps(c, 2);
+            if (rc) break;
+            CK(c, cudaEventRecord(e0, c->stream));
+            rc = launch_steps(c, steps);
+            if (rc) break;
+            CK(c, cudaEventRecord(e1, c->stream));
+            CK(c, cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(c, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / steps < best) { best = ms / steps; bc = k; bs = s; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->use_graphs = graphs0;
+    if (rc) return rc;
+    c->parity = parity0;
+    c->steps = steps0;
+    c->launches = launches0;
+    for (int i = 0; i < c->n; ++i)
+        CK(c, cudaMemcpy(c->h[i].pop[c->parity], snap[i].data(), snap[i].size(), cudaMemcpyHostToDevice));
+    CK(c, cudaMemset(c->d_status, 0, c->n * sizeof(int)));
+    rc = apply_schedule(c, bc, bs);
+    if (rc) return rc;
+    if (tile_config) *tile_config = bc;
+    if (schedule) *schedule = bs;
+    if (ms_per_step) *ms_per_step = best;
+    return LBM_OK;
+}
+
+int lbm_use_graphs(lbm_ctx* c, int on) {
+    if (!c) return LBM_EINVAL;
+    if (on && c->stream == nullptr) return fail(c, LBM_EINVAL, "CUDA graphs need a non-default stream%s");
+    c->use_graphs = on != 0;
+    if (!on) drop_graphs(c);
+    return LBM_OK;
+}
+
+long long lbm_steps_done(lbm_ctx* c) { return c ? c->steps : -1; }
+long long lbm_kernel_launches(lbm_ctx* c) { return c ? c->launches : -1; }
+
+int lbm_bytes_per_update(int precision) {
+    const int e = esize(precision);
+    return e ? 18 * e : LBM_EINVAL;
+}
+
+const char* lbm_last_error(lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// lbm_internal.cuh -- device data layout, per-instance descriptors and the
+// PTX helpers (mbarrier, TMA) shared by the sm_103a kernels of liblbm.
+//
+// HBM layout of one instance in precision T (float: deviations from
+// t_a rho_ref; double: same, rho_ref may be 0):
+//   pop[k][a][Y][X],  k in {0,1} the two time levels, a = 0..8,
+//   Y = y + GY (GY = 2 ghost rows above and below),
+//   X = x + GX (GX = 32 bytes / sizeof(T) ghost columns on the left, so an
+//   interior row starts on a 32-byte sector), row pitch a multiple of 32 B.
+// The array holds post-collision populations at their source node ("pull"
+// storage): the pre-collision f_a(x, t) is pop[a][x - e_a].  Ghost cells
+// hold periodic images, written by the step kernel for border nodes, so a
+// tile's halo is one rectangular TMA box with no wrap logic.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int GY = 2;          // ghost rows per side
+constexpr int kMaxSched = 3;   // CTA schedules known to lbm_set_schedule
+
+template <typename T> struct Prec;
+template <> struct Prec<float> { static constexpr int GX = 8; static constexpr int HX = 4; };
+template <> struct Prec<double> { static constexpr int GX = 4; static constexpr int HX = 2; };
+
+// Lattice velocity components e_a.
+__host__ __device__ constexpr int cx(int a) {
+    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int a) {
+    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+
+// Status bits of an instance (sticky until cleared or re-initialised).
+constexpr int ST_UNSTABLE = 1;
+constexpr int ST_TIMEOUT = 2;
+
+// Physics parameters in the kernel's precision.
+template <typename T> struct Phys {
+    int eos;            // LBM_EOS_*
+    unsigned flags;     // LBM_FLAG_*
+    T K, a, b, b4, RT, aalpha;   // EOS; b4 = b/4 (CS), aalpha = a alpha(T) (PR)
+    T A, kappa, G, two_over_G;   // Eq. 9, Eq. 23, Eq. 10
+    T s[9];             // Lambda
+    T hs[9];            // 1 - s/2, the forcing weight of Eq. 5
+    T c1, c2;           // C[1] = c1 tr Q, C[2] = c2 tr Q (Eq. 26)
+    T rho_ref;          // deviation reference
+    int interact;       // 0 when G == 0: no psi, F = Q = 0
+};
+
+// One lattice.  The two tensor maps come first: a CUtensorMap must sit on a
+// 64-byte boundary in global memory.
+struct alignas(128) Inst {
+    CUtensorMap tmap[2];     // 3-D maps {pitch, nyp, 9} of pop[0], pop[1]
+    void* pop[2];
+    int* status;
+    int nx, ny, pitch, nyp;  // pitch, nyp in elements
+    long long plane;         // pitch * nyp
+    Phys<float> pf;
+    Phys<double> pd;
+    int prec;                // LBM_FP32 / LBM_FP64
+    int pad_[3];
+};
+
+template <typename T> __device__ __forceinline__ const Phys<T>& phys(const Inst* I);
+template <> __device__ __forceinline__ const Phys<float>& phys<float>(const Inst* I) { return I->pf; }
+template <> __device__ __forceinline__ const Phys<double>& phys<double>(const Inst* I) { return I->pd; }
+
+// Pressure law (Eq. 21 / Eq. 29 / Carnahan-Starling); K scales the whole law.
+template <typename T> __device__ __forceinline__ T p_eos(const Phys<T>& P, T rho) {
+    if (P.eos == LBM_EOS_CS) {
+        T n = P.b4 * rho;
+        T q = T(1) - n;
+        T num = T(1) + n * (T(1) + n * (T(1) - n));
+        return P.K * (rho * P.RT * num / (q * q * q) - P.a * rho * rho);
+    } else if (P.eos == LBM_EOS_VDW) {
+        return P.K * (rho * P.RT / (T(1) - P.b * rho) - P.a * rho * rho);
+    } else {
+        T br = P.b * rho;
+        return P.K * (rho * P.RT / (T(1) - br) - P.aalpha * rho * rho / (T(1) + T(2) * br - br * br));
+    }
+}
+
+// Radicand of Eq. 10 with c = 1: psi^2 = 2 (p_EOS - rho/3) / G.
+template <typename T> __device__ __forceinline__ T psi_radicand(const Phys<T>& P, T rho) {
+    return P.two_over_G * (p_eos(P, rho) - rho * T(1.0 / 3.0));
+}
+
+// ---- PTX helpers --------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete, giving up after
+// timeout_ns of wall time.  Returns true when the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) return false;
+    }
+}
+
+// 3-D tiled TMA load of a box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// The tensor maps sit in global memory and the host rewrites them when the
+// tile shape changes: acquire them through the tensormap proxy before use.
+__device__ __forceinline__ void acquire_tmap(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+}  // namespace lbm
+
+// ---- host-side interfaces between the translation units -----------------
+namespace lbm {
+
+struct TileCfg { int bx, by, threads; };
+
+// Fused step (lbm_step.cu).
+int step_config_count(int prec);
+TileCfg step_config(int prec, int k);
+size_t step_smem_bytes(int prec, int k);
+cudaError_t step_prepare(int prec, int k);   // sets the dynamic smem attribute
+cudaError_t step_launch(int prec, int k, const Inst* d_insts, const int4* d_tiles, int ntiles,
+                        int parity, unsigned long long timeout_ns, cudaStream_t st);
+
+// Auxiliary kernels (lbm_aux.cu); `host` is the host copy of the descriptor.
+cudaError_t aux_init(const Inst& host, const Inst* d_inst, const double* rho, const double* ux,
+                     const double* uy, int parity, cudaStream_t st);
+cudaError_t aux_fill_ghosts(const Inst& host, const Inst* d_inst, int parity, cudaStream_t st);
+cudaError_t aux_gather_plane(const Inst& host, const Inst* d_inst, int parity, int a, double* out,
+                             cudaStream_t st);
+// field: 0 rho, 1 ux, 2 uy, 3 psi
+cudaError_t aux_field(const Inst& host, const Inst* d_inst, int parity, int field, double* out,
+                      cudaStream_t st);
+constexpr int kReduceBlocks = 304;   // 2 CTAs per SM of a 152-SM GB300: partial sums of FP64 reductions
+constexpr int kReduceSlots = 8;
+cudaError_t aux_measure(const Inst& host, const Inst* d_inst, int parity, double cx, double cy,
+                        double r_in, double r_out, double* partials, double* result,
+                        cudaStream_t st);
+cudaError_t aux_stats(const Inst& host, const Inst* d_inst, int parity, double* partials,
+                      double* result, cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,349 @@
+"""Thin ctypes binding of include/lbm.h.
+
+Argument marshalling only: every step of the method runs in the sm_103a
+kernels of liblbm.so.  PyTorch supplies the device buffer handed to
+lbm_create (``dev_buf``) and the CUDA stream; nothing here computes the
+method.  The module fails loudly when the library has not been built.
+
+The functions keep the C names (``lbm_create``, ``lbm_step``, ...); the
+``Lattice`` and ``Batch`` classes bundle a context with its buffer and stream.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EIO = 0, -1, -2, -3, -4, -5, -6
+LBM_FP32, LBM_FP64 = 1, 2
+LBM_EOS_CS, LBM_EOS_VDW, LBM_EOS_PR = 1, 2, 3
+LBM_FLAG_LI_EPS = 0x1
+LBM_FLAG_TEST_FORCE_TIMEOUT = 0x100
+LBM_MEASURE_N = 8
+
+_CODES = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA", LBM_EUNSTABLE: "EUNSTABLE",
+          LBM_ETIMEOUT: "ETIMEOUT", LBM_EIO: "EIO"}
+
+EXPORTS = [
+    "lbm_eos_pressure", "lbm_eos_critical", "lbm_eos_maxwell", "lbm_laplace_fit",
+    "lbm_required_bytes", "lbm_batch_required_bytes", "lbm_create", "lbm_batch_create", "lbm_destroy",
+    "lbm_set_params", "lbm_batch_set_params", "lbm_init_density", "lbm_batch_init_density",
+    "lbm_step", "lbm_sync", "lbm_status", "lbm_clear_status",
+    "lbm_read_fields", "lbm_batch_read_fields", "lbm_read_populations", "lbm_batch_read_populations",
+    "lbm_measure_pressure_jump", "lbm_batch_measure", "lbm_stats", "lbm_batch_stats",
+    "lbm_save", "lbm_load", "lbm_tile_config_count", "lbm_tile_config", "lbm_set_schedule",
+    "lbm_autotune", "lbm_use_graphs", "lbm_steps_done", "lbm_kernel_launches", "lbm_bytes_per_update",
+    "lbm_last_error",
+]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_CODES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class lbm_eos(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
+                ("K", ctypes.c_double), ("T", ctypes.c_double), ("omega", ctypes.c_double), ("Tc", ctypes.c_double)]
+
+
+@dataclass
+class Eos:
+    kind: int = LBM_EOS_CS
+    a: float = 1.0
+    b: float = 4.0
+    R: float = 1.0
+    K: float = 1.0
+    T: float = 0.0
+    omega: float = 0.0
+    Tc: float = 0.0
+
+    def c(self) -> lbm_eos:
+        return lbm_eos(int(self.kind), float(self.a), float(self.b), float(self.R), float(self.K), float(self.T),
+                       float(self.omega), float(self.Tc))
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load liblbm.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbm.so is not built at %s: run __graft_entry__.build() first" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    E = ctypes.POINTER(lbm_eos)
+    sig = {
+        "lbm_eos_pressure": ([E, ctypes.c_double, _dp], ctypes.c_int),
+        "lbm_eos_critical": ([E, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_eos_maxwell": ([E, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_laplace_fit": ([ctypes.c_int, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_required_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+        "lbm_batch_required_bytes": ([ctypes.c_int, _ip, _ip, ctypes.c_int], ctypes.c_size_t),
+        "lbm_create": ([ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp],
+                       ctypes.c_int),
+        "lbm_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip, ctypes.c_int, _vp, ctypes.c_size_t, _vp],
+                             ctypes.c_int),
+        "lbm_destroy": ([_vp], None),
+        "lbm_set_params": ([_vp, E, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_double,
+                            ctypes.c_uint], ctypes.c_int),
+        "lbm_batch_set_params": ([_vp, ctypes.c_int, E, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
+                                  ctypes.c_double, ctypes.c_uint], ctypes.c_int),
+        "lbm_init_density": ([_vp, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_batch_init_density": ([_vp, ctypes.c_int, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_step": ([_vp, ctypes.c_int], ctypes.c_int),
+        "lbm_sync": ([_vp], ctypes.c_int),
+        "lbm_status": ([_vp, ctypes.c_int], ctypes.c_int),
+        "lbm_clear_status": ([_vp], ctypes.c_int),
+        "lbm_read_fields": ([_vp, _dp, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_batch_read_fields": ([_vp, ctypes.c_int, _dp, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_read_populations": ([_vp, _dp], ctypes.c_int),
+        "lbm_batch_read_populations": ([_vp, ctypes.c_int, _dp], ctypes.c_int),
+        "lbm_measure_pressure_jump": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       _dp, _dp, _dp], ctypes.c_int),
+        "lbm_batch_measure": ([_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, _dp], ctypes.c_int),
+        "lbm_stats": ([_vp, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_batch_stats": ([_vp, ctypes.c_int, _dp], ctypes.c_int),
+        "lbm_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+        "lbm_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
+        "lbm_tile_config_count": ([ctypes.c_int], ctypes.c_int),
+        "lbm_tile_config": ([ctypes.c_int, ctypes.c_int, _ip, _ip, _ip], ctypes.c_int),
+        "lbm_set_schedule": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "lbm_autotune": ([_vp, ctypes.c_int, _ip, _ip, _dp], ctypes.c_int),
+        "lbm_use_graphs": ([_vp, ctypes.c_int], ctypes.c_int),
+        "lbm_steps_done": ([_vp], ctypes.c_longlong),
+        "lbm_kernel_launches": ([_vp], ctypes.c_longlong),
+        "lbm_bytes_per_update": ([ctypes.c_int], ctypes.c_int),
+        "lbm_last_error": ([_vp], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a, shape):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _check(ctx, rc: int):
+    if rc != LBM_OK:
+        msg = lib().lbm_last_error(ctx).decode() if ctx else ""
+        raise LbmError(rc, msg)
+    return rc
+
+
+# ---- host EOS helpers ----------------------------------------------------
+def lbm_eos_pressure(eos: Eos, rho: float) -> float:
+    p = ctypes.c_double()
+    _check(None, lib().lbm_eos_pressure(ctypes.byref(eos.c()), rho, ctypes.byref(p)))
+    return p.value
+
+
+def lbm_eos_critical(eos: Eos):
+    r, t, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(None, lib().lbm_eos_critical(ctypes.byref(eos.c()), ctypes.byref(r), ctypes.byref(t), ctypes.byref(p)))
+    return r.value, t.value, p.value
+
+
+def lbm_eos_maxwell(eos: Eos):
+    g, l, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(None, lib().lbm_eos_maxwell(ctypes.byref(eos.c()), ctypes.byref(g), ctypes.byref(l), ctypes.byref(p)))
+    return g.value, l.value, p.value
+
+
+def lbm_laplace_fit(dp: Sequence[float], R: Sequence[float]):
+    dp = np.ascontiguousarray(dp, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    s, c, r2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(None, lib().lbm_laplace_fit(len(dp), _ptr(dp), _ptr(R), ctypes.byref(s), ctypes.byref(c),
+                                       ctypes.byref(r2)))
+    return s.value, c.value, r2.value
+
+
+def lbm_required_bytes(nx: int, ny: int, precision: int) -> int:
+    return int(lib().lbm_required_bytes(nx, ny, precision))
+
+
+def lbm_batch_required_bytes(nx: Sequence[int], ny: Sequence[int], precision: int) -> int:
+    n = len(nx)
+    ax = (ctypes.c_int * n)(*nx)
+    ay = (ctypes.c_int * n)(*ny)
+    return int(lib().lbm_batch_required_bytes(n, ax, ay, precision))
+
+
+def lbm_tile_configs(precision: int):
+    out = []
+    for k in range(lib().lbm_tile_config_count(precision)):
+        bx, by, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib().lbm_tile_config(precision, k, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(nt))
+        out.append((bx.value, by.value, nt.value))
+    return out
+
+
+DEFAULT_S = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
+
+
+class Batch:
+    """A context of n independent periodic lattices stepped together
+    (lbm_batch_create).  Device memory is one torch uint8 tensor; work runs
+    on a dedicated torch CUDA stream unless one is given."""
+
+    def __init__(self, nx: Sequence[int], ny: Sequence[int], precision: int = LBM_FP32, stream=None,
+                 device_buffer: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        L = lib()
+        self.nx = [int(v) for v in nx]
+        self.ny = [int(v) for v in ny]
+        self.n = len(self.nx)
+        self.precision = precision
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        nbytes = lbm_batch_required_bytes(self.nx, self.ny, precision)
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "invalid lattice shape")
+        self._buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda") if device_buffer else None
+        self.ctx = ctypes.c_void_p()
+        ax = (ctypes.c_int * self.n)(*self.nx)
+        ay = (ctypes.c_int * self.n)(*self.ny)
+        buf = ctypes.c_void_p(self._buf.data_ptr()) if self._buf is not None else None
+        rc = L.lbm_batch_create(ctypes.byref(self.ctx), self.n, ax, ay, precision, buf, nbytes,
+                                ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_batch_create failed")
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lib().lbm_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+        self._buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _c(self, rc):
+        return _check(self.ctx, rc)
+
+    def set_params(self, i: int, eos: Eos, A: float, kappa: float, G: float = -1.0, s: Sequence[float] = DEFAULT_S,
+                   rho_ref: float = 0.0, flags: int = 0):
+        sv = (ctypes.c_double * 9)(*[float(v) for v in s])
+        self._c(lib().lbm_batch_set_params(self.ctx, i, ctypes.byref(eos.c()), A, kappa, G, sv, rho_ref, flags))
+
+    def init_density(self, i: int, rho, ux=None, uy=None):
+        shape = (self.ny[i], self.nx[i])
+        r, u, v = _f64(rho, shape), _f64(ux, shape), _f64(uy, shape)
+        self._c(lib().lbm_batch_init_density(self.ctx, i, _ptr(r), _ptr(u), _ptr(v)))
+
+    def step(self, n: int):
+        self._c(lib().lbm_step(self.ctx, int(n)))
+
+    def sync(self):
+        self._c(lib().lbm_sync(self.ctx))
+
+    def status(self, i: int) -> int:
+        return lib().lbm_status(self.ctx, i)
+
+    def clear_status(self):
+        self._c(lib().lbm_clear_status(self.ctx))
+
+    def read_fields(self, i: int = 0, which=("rho", "ux", "uy", "psi")):
+        shape = (self.ny[i], self.nx[i])
+        outs = {k: np.empty(shape) for k in which}
+        self._c(lib().lbm_batch_read_fields(self.ctx, i, *[_ptr(outs.get(k)) for k in ("rho", "ux", "uy", "psi")]))
+        return outs
+
+    def read_populations(self, i: int = 0) -> np.ndarray:
+        f = np.empty((9, self.ny[i], self.nx[i]))
+        self._c(lib().lbm_batch_read_populations(self.ctx, i, _ptr(f)))
+        return f
+
+    def measure(self, i: int, cx: float, cy: float, r_in: float, r_out: float) -> dict:
+        o = np.empty(LBM_MEASURE_N)
+        self._c(lib().lbm_batch_measure(self.ctx, i, cx, cy, r_in, r_out, _ptr(o)))
+        keys = ("p_in", "p_out", "rho_in", "rho_out", "R_eq", "mass", "n_in", "n_out")
+        d = dict(zip(keys, (float(v) for v in o)))
+        d["dp"] = d["p_in"] - d["p_out"]
+        d["sigma"] = d["dp"] * d["R_eq"]
+        return d
+
+    def stats(self, i: int = 0) -> dict:
+        o = np.empty(5)
+        self._c(lib().lbm_batch_stats(self.ctx, i, _ptr(o)))
+        return dict(zip(("mass", "mom_x", "mom_y", "ke", "umax"), (float(v) for v in o)))
+
+    def save(self, path: str):
+        self._c(lib().lbm_save(self.ctx, path.encode()))
+
+    def load(self, path: str):
+        self._c(lib().lbm_load(self.ctx, path.encode()))
+
+    def set_schedule(self, tile_config: int, schedule: int = 0):
+        self._c(lib().lbm_set_schedule(self.ctx, tile_config, schedule))
+
+    def autotune(self, steps: int = 20):
+        k, s, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._c(lib().lbm_autotune(self.ctx, steps, ctypes.byref(k), ctypes.byref(s), ctypes.byref(ms)))
+        return k.value, s.value, ms.value
+
+    def use_graphs(self, on: bool = True):
+        self._c(lib().lbm_use_graphs(self.ctx, int(bool(on))))
+
+    @property
+    def steps_done(self) -> int:
+        return int(lib().lbm_steps_done(self.ctx))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(lib().lbm_kernel_launches(self.ctx))
+
+
+class Lattice(Batch):
+    """One periodic nx x ny lattice (lbm_create); instance-0 shorthands."""
+
+    def __init__(self, nx: int, ny: int, precision: int = LBM_FP32, stream=None, device_buffer: bool = True):
+        super().__init__([nx], [ny], precision, stream, device_buffer)
+
+    def set_params(self, eos: Eos, A: float, kappa: float, G: float = -1.0, s: Sequence[float] = DEFAULT_S,
+                   rho_ref: float = 0.0, flags: int = 0):
+        super().set_params(0, eos, A, kappa, G, s, rho_ref, flags)
+
+    def init_density(self, rho, ux=None, uy=None):
+        super().init_density(0, rho, ux, uy)
+
+    def measure_pressure_jump(self, cx: float, cy: float, r_in: float, r_out: float) -> dict:
+        return self.measure(0, cx, cy, r_in, r_out)

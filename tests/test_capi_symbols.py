@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every function include/lbm.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def liblbm():
+    from paper_1412_7228_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_function_is_exported(liblbm):
+    names = declared_functions()
+    assert len(names) >= 30
+    missing = [n for n in names if not hasattr(liblbm, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_1412_7228_gb300 import lbm
+    assert sorted(lbm.EXPORTS) == declared_functions()
+
+
+def test_host_only_calls_work_without_a_gpu(liblbm):
+    import paper_1412_7228_gb300 as P
+    assert P.lbm_required_bytes(64, 64, P.LBM_FP32) > 0
+    assert P.lbm_required_bytes(1, 64, P.LBM_FP32) == 0          # nx < 2 is rejected
+    assert P.lbm_required_bytes(64, 64, 3) == 0                  # unknown precision
+    assert liblbm.lbm_bytes_per_update(P.LBM_FP32) == 72
+    assert liblbm.lbm_bytes_per_update(P.LBM_FP64) == 144
+    cfgs = P.lbm_tile_configs(P.LBM_FP32)
+    assert (64, 16, 256) in cfgs
+
+
+def test_product_eos_helpers_agree_with_the_oracle():
+    """The library's own critical-point and Maxwell solvers (host C++) against
+    the oracle's independent scipy ones."""
+    import warnings
+    warnings.filterwarnings("ignore")
+    import oracle as O
+    from oracle import analysis as An
+    import paper_1412_7228_gb300 as P
+    e = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
+    rc, Tc, pc = P.lbm_eos_critical(e)
+    orc = An.critical_point(O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0))
+    assert abs(Tc / orc[1] - 1) < 1e-10 and abs(rc / orc[0] - 1) < 1e-6
+    for tr in (0.6, 0.7, 0.8):
+        e.T = tr * Tc
+        g, l, p0 = P.lbm_eos_maxwell(e)
+        og, ol, op0 = An.maxwell(An.with_T(O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0), tr * orc[1]))
+        assert abs(g / og - 1) < 1e-8 and abs(l / ol - 1) < 1e-8
+    for rho in (0.01, 0.2, 0.4):
+        ref = O.pressure(An.with_T(O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0), e.T), [rho])[0]
+        assert abs(P.lbm_eos_pressure(e, rho) - ref) < 1e-15
+    s, c, r2 = P.lbm_laplace_fit([0.3, 0.2, 0.15], [10.0, 15.0, 20.0])
+    assert abs(s - 3.0) < 1e-12 and abs(c) < 1e-12 and abs(r2 - 1) < 1e-12

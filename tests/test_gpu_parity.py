@@ -1,0 +1,290 @@
+"""GPU-vs-oracle parity of the fused sm_103a step, through the C ABI.
+
+Tolerances (derivation in DESIGN.md, "Parity tolerances"):
+  FP64: the kernel evaluates the same formulas in a different order (unrolled
+        moments, fused multiply-adds); after n steps of a dissipative update
+        the populations agree to ~1e-15 n relative -> 1e-12 for n <= 100.
+  FP32: populations are stored as deviations from t_a rho_ref and updated in
+        FP32 (unit roundoff 6e-8); about 30 roundings feed each population per
+        step and errors of a stable step do not grow, so 50 steps stay within
+        2e-5 of the largest population; density fields within 1e-4 relative.
+"""
+import warnings
+
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+import oracle as O
+from oracle import analysis as An
+
+warnings.filterwarnings("ignore", category=Warning, module="scipy")
+
+pytestmark = pytest.mark.gpu
+
+S_CFG = [1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0]
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1412_7228_gb300 as P
+    P.lib()
+    return P
+
+
+def cs_case(P, tr=0.7, A=-0.85, kappa=0.3):
+    eos = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
+    _, Tc, _ = P.lbm_eos_critical(eos)
+    eos.T = tr * Tc
+    rg, rl, _ = P.lbm_eos_maxwell(eos)
+    op = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, T=eos.T, A=A, kappa=kappa, G=-1.0, s=list(S_CFG))
+    return eos, op, rg, rl
+
+
+def oracle_run(op, rho0, steps):
+    f = O.init_equilibrium(rho0)
+    O.step(op, f, steps)
+    return f
+
+
+def gpu_run(P, prec, eos, op, rho0, steps, rho_ref, cfg=None, sched=0, graphs=False):
+    ny, nx = rho0.shape
+    lat = P.Lattice(nx, ny, prec)
+    if cfg is not None:
+        lat.set_schedule(cfg, sched)
+    lat.set_params(eos, op.A, op.kappa, G=op.G, s=op.s, rho_ref=rho_ref)
+    lat.init_density(rho0)
+    if graphs:
+        lat.use_graphs(True)
+    lat.step(steps)
+    lat.sync()
+    f = lat.read_populations()
+    lat.close()
+    return f
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 1e-12), (1, 2e-5)])
+@pytest.mark.parametrize("shape", [(100, 70), (64, 64), (130, 36)])
+def test_droplet_populations_match_oracle(P, prec, tol, shape):
+    """Several tiles and ragged tails in x and y, 50 steps."""
+    nx, ny = shape
+    eos, op, rg, rl = cs_case(P)
+    rho0 = I.droplet_density(nx, ny, min(nx, ny) / 4, rl, rg)
+    ref = oracle_run(op, rho0, 50)
+    got = gpu_run(P, prec, eos, op, rho0, 50, rho_ref=rg)
+    assert rel(got, ref) <= tol
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (6, 6), (8, 5), (2, 2), (3, 7), (33, 17)])
+def test_tiny_and_odd_domains(P, shape):
+    nx, ny = shape
+    eos, op, rg, rl = cs_case(P, kappa=0.5)
+    rho0 = I.spinodal_density(nx, ny, rho0=0.25, amp=0.05, seed=nx * 131 + ny)
+    ref = oracle_run(op, rho0, 10)
+    assert rel(gpu_run(P, P.LBM_FP64, eos, op, rho0, 10, rho_ref=0.25), ref) <= 1e-12
+    assert rel(gpu_run(P, P.LBM_FP32, eos, op, rho0, 10, rho_ref=0.25), ref) <= 2e-5
+
+
+def test_every_tile_config_and_graphs_are_bit_identical(P):
+    """The per-node arithmetic does not depend on the tiling: every tile
+    configuration, CTA schedule and the CUDA-graph path give the same bits."""
+    eos, op, rg, rl = cs_case(P)
+    rho0 = I.droplet_density(90, 75, 20, rl, rg)
+    for prec in (P.LBM_FP64, P.LBM_FP32):
+        base = gpu_run(P, prec, eos, op, rho0, 70, rho_ref=rg, cfg=0)
+        for k in range(len(P.lbm_tile_configs(prec))):
+            assert np.array_equal(gpu_run(P, prec, eos, op, rho0, 70, rho_ref=rg, cfg=k), base), (prec, k)
+        assert np.array_equal(gpu_run(P, prec, eos, op, rho0, 70, rho_ref=rg, graphs=True), base)
+
+
+def test_vdw_flat_interface_matches_oracle_and_table1(P, golden):
+    """The paper's flat-interface case (Table 1) on the GPU in FP64: same
+    populations as the oracle after 2000 steps, and after 15000 steps the
+    printed densities to all digits (s = 1, reading R14)."""
+    eos = P.Eos(kind=P.LBM_EOS_VDW, a=9 / 49, b=2 / 21, R=1.0, K=0.3)
+    _, Tc, _ = P.lbm_eos_critical(eos)
+    eos.T = 0.9 * Tc
+    op = O.Params(eos=O.EOS_VDW, a=9 / 49, b=2 / 21, R=1.0, K=0.3, T=eos.T, A=-0.5, kappa=0.5, s=[1.0] * 9)
+    rho0 = I.slab_density(128, 4, 5.8, 1.47, width=4.0)
+    ref = oracle_run(op, rho0, 2000)
+    assert rel(gpu_run(P, P.LBM_FP64, eos, op, rho0, 2000, rho_ref=1.47), ref) <= 1e-11
+    lat = P.Lattice(128, 4, P.LBM_FP64)
+    lat.set_params(eos, -0.5, 0.5, G=-1.0, s=[1.0] * 9, rho_ref=1.47)
+    lat.init_density(rho0)
+    lat.step(15000)
+    rho = lat.read_fields(which=("rho",))["rho"]
+    rl, rg = An.slab_densities(rho)
+    t1 = golden["table1_flat_interface"]
+    assert round(rl, 5) == t1["rho_l"] and round(rg, 5) == t1["rho_g"]
+
+
+def test_static_droplet_64_after_10000_steps(P):
+    """64x64 Carnahan-Starling droplet, R = 15, T = 0.7 Tc, kappa = 0,
+    10^4 steps: density max relative error <= 1e-10 (FP64), <= 1e-4 (FP32)."""
+    eos, op, rg, rl = cs_case(P, kappa=0.0)
+    rho0 = I.droplet_density(64, 64, 15, rl, rg)
+    f_ref = oracle_run(op, rho0, 10000)
+    rho_ref_field = O.macro(op, f_ref)[0]
+    for prec, tol in ((P.LBM_FP64, 1e-10), (P.LBM_FP32, 1e-4)):
+        lat = P.Lattice(64, 64, prec)
+        lat.set_params(eos, op.A, 0.0, s=S_CFG, rho_ref=rg)
+        lat.init_density(rho0)
+        lat.step(10000)
+        rho = lat.read_fields(which=("rho",))["rho"]
+        lat.close()
+        err = float(np.abs(rho / rho_ref_field - 1).max())
+        assert err <= tol, (prec, err)
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 1e-10), (1, 1e-4)])
+def test_fields_measure_and_stats_match_oracle(P, prec, tol):
+    eos, op, rg, rl = cs_case(P)
+    nx, ny = 80, 64
+    rho0 = I.droplet_density(nx, ny, 16, rl, rg)
+    f_ref = oracle_run(op, rho0, 300)
+    r, ux, uy, psi, Fx, Fy = O.macro(op, f_ref)
+    lat = P.Lattice(nx, ny, prec)
+    lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+    lat.init_density(rho0)
+    lat.step(300)
+    fl = lat.read_fields()
+    assert rel(fl["rho"], r) <= tol and rel(fl["psi"], psi) <= tol
+    umax = np.hypot(ux, uy).max()
+    assert np.abs(fl["ux"] - ux).max() <= 100 * tol * umax + 1e-12
+    m = lat.measure_pressure_jump(nx / 2, ny / 2, 8, 24)
+    d = An.pressure_jump(op, r, nx / 2, ny / 2, 8, 24)
+    for k in ("p_in", "p_out", "rho_in", "rho_out", "R_eq"):
+        assert abs(m[k] / d[k] - 1) <= tol, k
+    st = lat.stats()
+    assert abs(st["mass"] / r.sum() - 1) <= tol
+    assert abs(st["umax"] / umax - 1) <= 100 * tol
+    assert abs(st["ke"] / (0.5 * r * (ux * ux + uy * uy)).sum() - 1) <= 100 * tol
+    lat.close()
+
+
+def test_g_zero_shear_wave_matches_oracle(P):
+    """G = 0: no psi, F = Q = 0 (reading R11)."""
+    L = 64
+    y = np.arange(L)
+    ux = np.broadcast_to((1e-3 * np.sin(2 * np.pi * y / L))[:, None], (L, 32)).copy()
+    op = O.Params(G=0.0, s=[1, 1.1, 1.1, 1, 1.1, 1, 1.1, 1.3, 1.3], eos=O.EOS_CS, a=1, b=4, R=1, K=1, T=0.07)
+    f = O.init_equilibrium(np.ones((L, 32)), ux, np.zeros_like(ux))
+    O.step(op, f, 200)
+    eos = P.Eos(kind=P.LBM_EOS_CS, a=1, b=4, R=1, K=1, T=0.07)
+    lat = P.Lattice(32, L, P.LBM_FP64)
+    lat.set_params(eos, op.A, 0.0, G=0.0, s=op.s, rho_ref=1.0)
+    lat.init_density(np.ones((L, 32)), ux, np.zeros_like(ux))
+    lat.step(200)
+    assert rel(lat.read_populations(), f) <= 1e-12
+    lat.close()
+
+
+def test_batch_equals_separate_runs(P):
+    """Uneven instances stepped together in one launch per step give the
+    same bits as each instance alone, for every CTA schedule."""
+    eos, op, rg, rl = cs_case(P)
+    shapes = [(96, 96), (40, 72), (130, 50)]
+    rhos = [I.droplet_density(nx, ny, min(nx, ny) / 4, rl, rg) for nx, ny in shapes]
+    for prec in (P.LBM_FP64, P.LBM_FP32):
+        solo = [gpu_run(P, prec, eos, op, r, 40, rho_ref=rg) for r in rhos]
+        for sched in (0, 1, 2):
+            b = P.Batch([s[0] for s in shapes], [s[1] for s in shapes], prec)
+            b.set_schedule(0, sched)
+            for i, r in enumerate(rhos):
+                b.set_params(i, eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+                b.init_density(i, r)
+            b.step(40)
+            outs = [b.read_populations(i) for i in range(len(shapes))]
+            b.close()
+            for i in range(len(shapes)):
+                assert np.array_equal(outs[i], solo[i]), (prec, sched, i)
+
+
+def test_checkpoint_resume_is_bit_identical(P, tmp_path):
+    eos, op, rg, rl = cs_case(P)
+    rho0 = I.droplet_density(70, 50, 12, rl, rg)
+    path = str(tmp_path / "ck.bin")
+    lat = P.Lattice(70, 50, P.LBM_FP32)
+    lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+    lat.init_density(rho0)
+    lat.step(25)
+    lat.save(path)
+    lat.step(25)
+    straight = lat.read_populations()
+    lat.close()
+    lat2 = P.Lattice(70, 50, P.LBM_FP32)
+    lat2.load(path)
+    assert lat2.steps_done == 25
+    lat2.step(25)
+    assert np.array_equal(lat2.read_populations(), straight)
+    lat2.close()
+
+
+def test_autotune_keeps_the_state(P):
+    eos, op, rg, rl = cs_case(P)
+    rho0 = I.droplet_density(128, 96, 20, rl, rg)
+    ref = gpu_run(P, P.LBM_FP32, eos, op, rho0, 30, rho_ref=rg)
+    lat = P.Lattice(128, 96, P.LBM_FP32)
+    lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+    lat.init_density(rho0)
+    k, s, ms = lat.autotune(5)
+    assert 0 <= k < len(P.lbm_tile_configs(P.LBM_FP32)) and ms > 0
+    lat.step(30)
+    assert np.array_equal(lat.read_populations(), ref)
+    lat.close()
+
+
+def test_density_outside_psi_domain_reports_unstable(P):
+    """R18: a density beyond the EOS's psi domain is reported, not clamped."""
+    eos, op, rg, rl = cs_case(P)
+    rho0 = I.droplet_density(32, 32, 6, rl, rg)
+    rho0[16, 16] = 0.7            # rho/3 - p_EOS < 0 for the CS law here
+    lat = P.Lattice(32, 32, P.LBM_FP32)
+    lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+    lat.init_density(rho0)
+    lat.step(1)
+    with pytest.raises(P.LbmError) as ei:
+        lat.sync()
+    assert ei.value.code == -4
+    lat.close()
+
+
+def test_nan_initial_field_is_rejected(P):
+    eos, op, rg, rl = cs_case(P)
+    rho0 = I.droplet_density(16, 16, 4, rl, rg)
+    rho0[3, 3] = np.nan
+    lat = P.Lattice(16, 16, P.LBM_FP32)
+    lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+    with pytest.raises(P.LbmError) as ei:
+        lat.init_density(rho0)
+    assert ei.value.code == -1
+    lat.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(P):
+    """A barrier phase nothing completes: every CTA gives up after its
+    limit, the status reads ETIMEOUT, and the context keeps working."""
+    eos, op, rg, rl = cs_case(P)
+    rho0 = I.droplet_density(64, 32, 8, rl, rg)
+    lat = P.Lattice(64, 32, P.LBM_FP32)
+    lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg, flags=P.LBM_FLAG_TEST_FORCE_TIMEOUT)
+    lat.init_density(rho0)
+    lat.step(1)
+    with pytest.raises(P.LbmError) as ei:
+        lat.sync()
+    assert ei.value.code == -5
+    lat.clear_status()
+    lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg, flags=0)
+    lat.init_density(rho0)
+    lat.step(10)
+    lat.sync()
+    ref = oracle_run(op, rho0, 10)
+    assert rel(lat.read_populations(), ref) <= 2e-5
+    lat.close()
