@@ -226,13 +226,14 @@ def run_ours(args):
     N = nx * ny
     rho0 = I.spinodal_density(nx, ny, RHO0, 0.01, SEED)
 
-    lat = make_lattice(P, nx, ny, P.LBM_FP32, rho0)
-    tile = None
+    prec = P.LBM_FP32 if args.precision == "fp32" else P.LBM_FP64
+    lat = make_lattice(P, nx, ny, prec, rho0)
     if args.autotune:
         k, s, ms = lat.autotune(10)
-        tile = P.lbm_tile_configs(P.LBM_FP32)[k]
     else:
-        tile = P.lbm_tile_configs(P.LBM_FP32)[0]
+        k = args.tile if args.tile is not None else (0 if prec == P.LBM_FP32 else 1)
+        lat.set_schedule(k, 0)
+    tile = P.lbm_tile_configs(prec)[k]
     lat.use_graphs(True)
     launches0 = lat.kernel_launches
     lat.step(args.warmup)
@@ -262,17 +263,17 @@ def run_ours(args):
     mlups = ws * N * args.steps / t / 1e6
     avg_launch = t / args.steps
     peak, peak_kind = measured_peak()
-    bpu = 72
+    bpu = 72 if prec == P.LBM_FP32 else 144
     achieved = bpu * N / avg_launch / 1e9
-    traffic = kernel_traffic("fp32")
+    traffic = kernel_traffic(args.precision)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": bpu,
-            "kernel": "lbm::k_step<float,%d,%d,%d>" % tuple(tile)}
+            "kernel": "lbm::k_step<%s,%d,%d,%d,%d>" % ((("float",) if prec == P.LBM_FP32 else ("double",)) + tuple(tile))}
     lat.close()
 
     # ---- FP64 on the same workload (fewer steps: it is FP64-ALU bound) ----
     fp64 = None
-    if not args.no_fp64:
+    if not args.no_fp64 and prec == P.LBM_FP32:
         lat64 = make_lattice(P, nx, ny, P.LBM_FP64, rho0)
         lat64.use_graphs(True)
         lat64.step(min(args.warmup, 10))
@@ -293,7 +294,8 @@ def run_ours(args):
         eos = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
         _, Tc, _ = P.lbm_eos_critical(eos)
         eos.T = TR_CFG * Tc
-        lat = P.Lattice(nx, ny, P.LBM_FP32)
+        lat = P.Lattice(nx, ny, prec)
+        lat.set_schedule(k, 0)
         lat.set_params(eos, A_CFG, KAPPA_CFG, G=-1.0, s=S_CFG, rho_ref=RHO0)
         lat.use_graphs(True)
         lat.init_density(host_rho)
@@ -323,8 +325,9 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1000.0 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(nx, ny, "fp32", {"tile": list(tile), "graphs": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == P.LBM_FP32 else "f64",
+            "data": "synthetic",
+            "config": workload_config(nx, ny, args.precision, {"tile": list(tile), "graphs": True,
                                                        "parallelism": "replicas" if ws > 1 else "single"}),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "fp64": fp64, "status_ok": status_ok,
@@ -344,6 +347,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--ny", type=int, default=4096)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--tile", type=int, default=None,
+                    help="tile configuration index (lbm_tile_config); default 0 (FP32) or 1 (FP64)")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

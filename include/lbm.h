@@ -182,9 +182,12 @@ int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);
 
 /* Tile configurations of the fused step kernel for this precision: returns
- * their number; for index k writes tile width, height and threads per CTA. */
+ * their number; for index k writes tile width, height, threads per CTA and
+ * pipeline stages (1: one tile per CTA; 2: persistent CTAs that prefetch the
+ * next tile's TMA box while colliding the current one).  Any pointer may be
+ * NULL. */
 int lbm_tile_config_count(int precision);
-int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads);
+int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads, int* stages);
 /* Select tile configuration k and CTA schedule (0: instance-major row
  * order, 1: tiles of all instances interleaved, 2: largest instance first). */
 int lbm_set_schedule(lbm_ctx* ctx, int tile_config, int schedule);

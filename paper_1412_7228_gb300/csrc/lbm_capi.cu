@@ -900,12 +900,13 @@ int lbm_tile_config_count(int precision) {
     return lbm::step_config_count(precision);
 }
 
-int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads) {
+int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads, int* stages) {
     if (esize(precision) == 0 || k < 0 || k >= lbm::step_config_count(precision)) return LBM_EINVAL;
     const lbm::TileCfg t = lbm::step_config(precision, k);
     if (bx) *bx = t.bx;
     if (by) *by = t.by;
     if (threads) *threads = t.threads;
+    if (stages) *stages = t.stages;
     return LBM_OK;
 }
 

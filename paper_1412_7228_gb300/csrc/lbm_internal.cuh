@@ -163,7 +163,7 @@ __device__ __forceinline__ void acquire_tmap(const CUtensorMap* map) {
 // ---- host-side interfaces between the translation units -----------------
 namespace lbm {
 
-struct TileCfg { int bx, by, threads; };
+struct TileCfg { int bx, by, threads, stages; };
 
 // Fused step (lbm_step.cu).
 int step_config_count(int prec);

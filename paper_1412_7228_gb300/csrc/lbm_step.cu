@@ -23,8 +23,9 @@
 namespace lbm {
 namespace {
 
-template <typename T, int BX_, int BY_, int NT_> struct Geom {
+template <typename T, int BX_, int BY_, int NT_, int NBUF_> struct Geom {
     static constexpr int BX = BX_, BY = BY_, NT = NT_;
+    static constexpr int NBUF = NBUF_;          // 1: one tile per CTA; 2: persistent, double-buffered
     static constexpr int HX = Prec<T>::HX;      // halo columns in the box (16 bytes)
     static constexpr int GX = Prec<T>::GX;      // ghost columns in HBM (32 bytes)
     static constexpr int WB = BX + 2 * HX;      // box width
@@ -35,31 +36,89 @@ template <typename T, int BX_, int BY_, int NT_> struct Geom {
     static constexpr int TY = NT / BX;          // thread rows
     static constexpr int ROWS = BY / TY;        // nodes per thread
     static constexpr size_t box_bytes = size_t(9) * PB * sizeof(T);
-    static constexpr size_t psi_off = (box_bytes + 127) / 128 * 128;
-    static constexpr size_t smem = psi_off + size_t(WP) * HP * sizeof(T);
+    static constexpr size_t buf_stride = (box_bytes + 127) / 128 * 128;      // box buffers
+    static constexpr size_t psi_off = NBUF * buf_stride;
+    static constexpr size_t psi_stride = (size_t(WP) * HP * sizeof(T) + 127) / 128 * 128;   // psi tiles
+    static constexpr size_t smem = psi_off + NBUF * psi_stride;
     static_assert(NT % BX == 0 && BY % TY == 0, "thread layout must tile the block");
     static_assert(WB <= 256 && HB <= 256, "TMA box dimensions are limited to 256");
     static_assert((WB * sizeof(T)) % 16 == 0, "TMA box rows must be a multiple of 16 bytes");
+    static_assert(BX >= 2, "the ring's extra columns are taken by threads tx = 0, 1");
 };
 
+// sum_a f_a grouped so that the result is invariant under the lattice's
+// mirror symmetries (x -> -x swaps 1<->3, 5<->6, 7<->8; y -> -y swaps 2<->4,
+// 5<->8, 6<->7): with commutative rounding a mirror-symmetric state stays
+// bitwise mirror-symmetric, so rounding cannot push a symmetric drop off its
+// centre (translation is a neutral mode of a static droplet).
+template <typename T> __device__ __forceinline__ T rho_dev(const T (&f)[9]) {
+    const T Sa = (f[1] + f[3]) + (f[2] + f[4]);
+    const T Sd = (f[5] + f[7]) + (f[6] + f[8]);
+    return f[0] + Sa + Sd;
+}
+
+// Product rounded on its own: never fused into an FMA with a neighbouring
+// add.  Used where a mirror or the x<->y transpose swaps two product terms
+// (p1^2 + p3^2, rho u_x^2 + rho u_y^2, ...): fma(a, a, b*b) is not
+// symmetric in a and b, a sum of two rounded products is.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Moment-space collision of one node in deviation form (Eqs. 2-6, 25, 26).
+// Every expression maps onto itself (or its negative) under the mirrors
+// above, which keeps symmetric states symmetric to the last bit.
 // f: pre-collision f_a - t_a rho_ref; out: post-collision, same form.
+// Division, reciprocal and square root of the step.  FP32 uses the
+// hardware approximations (a couple of ulp, far inside the FP32 error
+// budget of the stored populations); FP64 keeps IEEE operations.
+template <typename T> struct Fast;
+template <> struct Fast<float> {
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
+    static __device__ __forceinline__ float sqrt(float a) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
+};
+template <> struct Fast<double> {
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+    static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
+};
+
+// The parameters one node needs, copied into registers once per tile (the
+// descriptor lives in global memory, and the compiler may not keep values
+// read through it across the node loop's stores).
+// FP32 keeps them as values; FP64, bound by its FP64 pipe rather than by
+// issue slots, keeps references and spends its registers on occupancy.
+template <typename T, typename V> struct RegsOf {
+    V s1, s2, s4, s6, s7, s8, hs1, hs2, hs4, hs6, hs7, hs8, c1, c2, rho_ref;
+    __device__ __forceinline__ explicit RegsOf(const Phys<T>& P)
+        : s1(P.s[1]), s2(P.s[2]), s4(P.s[4]), s6(P.s[6]), s7(P.s[7]), s8(P.s[8]), hs1(P.hs[1]),
+          hs2(P.hs[2]), hs4(P.hs[4]), hs6(P.hs[6]), hs7(P.hs[7]), hs8(P.hs[8]), c1(P.c1), c2(P.c2),
+          rho_ref(P.rho_ref) {}
+};
+template <typename T> struct RegsSel { using type = RegsOf<T, const T&>; };
+template <> struct RegsSel<float> { using type = RegsOf<float, float>; };
+template <typename T> using Regs = typename RegsSel<T>::type;
+
 template <typename T>
-__device__ __forceinline__ void collide(const Phys<T>& P, const T (&f)[9], T Fx, T Fy, T Qxx, T Qyy,
+__device__ __forceinline__ void collide(const Regs<T>& P, const T (&f)[9], T Fx, T Fy, T Qxx, T Qyy,
                                         T Qxy, T (&out)[9]) {
     const T Sa = (f[1] + f[3]) + (f[2] + f[4]);
     const T Sd = (f[5] + f[7]) + (f[6] + f[8]);
-    const T rt = f[0] + Sa + Sd;                       // rho - rho_ref
+    const T rt = f[0] + Sa + Sd;                       // rho - rho_ref, as rho_dev()
     const T rho = P.rho_ref + rt;
-    const T inv = T(1) / rho;
+    const T inv = Fast<T>::rcp(rho);
     const T d13 = f[1] - f[3], d24 = f[2] - f[4];
     const T Dxd = (f[5] - f[7]) + (f[8] - f[6]);
     const T Dyd = (f[5] - f[7]) + (f[6] - f[8]);
     const T jx = d13 + Dxd, jy = d24 + Dyd;
     const T rux = jx + T(0.5) * Fx, ruy = jy + T(0.5) * Fy;   // rho v = j + F/2
     const T ux = rux * inv, uy = ruy * inv;
-    const T ru2 = rux * ux + ruy * uy;                 // rho |v|^2
-    const T vF = ux * Fx + uy * Fy;
+    const T ru2 = mul_rn(rux, ux) + mul_rn(ruy, uy);   // rho |v|^2
+    const T vF = mul_rn(ux, Fx) + mul_rn(uy, Fy);
     const T trQ = Qxx + Qyy;
 
     const T m1 = T(2) * Sd - Sa - T(4) * f[0];
@@ -71,18 +130,25 @@ __device__ __forceinline__ void collide(const Phys<T>& P, const T (&f)[9], T Fx,
 
     const T e1 = T(3) * ru2 - T(2) * rt;               // m_eq deviations (Eq. 4)
     const T e2 = rt - T(3) * ru2;
-    const T ms1 = m1 - P.s[1] * (m1 - e1) + P.hs[1] * (T(6) * vF) + P.c1 * trQ;
-    const T ms2 = m2 - P.s[2] * (m2 - e2) - P.hs[2] * (T(6) * vF) + P.c2 * trQ;
+    const T ms1 = m1 - P.s1 * (m1 - e1) + P.hs1 * (T(6) * vF) + P.c1 * trQ;
+    const T ms2 = m2 - P.s2 * (m2 - e2) - P.hs2 * (T(6) * vF) + P.c2 * trQ;
     const T ms3 = jx + Fx;                             // = m3 - s_j (m3 - rho v_x) + (1 - s_j/2) F_x
-    const T ms4 = m4 - P.s[4] * (m4 + rux) - P.hs[4] * Fx;
+    const T ms4 = m4 - P.s4 * (m4 + rux) - P.hs4 * Fx;
     const T ms5 = jy + Fy;
-    const T ms6 = m6 - P.s[6] * (m6 + ruy) - P.hs[6] * Fy;
-    const T ms7 = m7 - P.s[7] * (m7 - (rux * ux - ruy * uy)) + P.hs[7] * (T(2) * (ux * Fx - uy * Fy)) -
-                  P.s[7] * (Qxx - Qyy);
-    const T ms8 = m8 - P.s[8] * (m8 - rux * uy) + P.hs[8] * (ux * Fy + uy * Fx) - P.s[8] * Qxy;
+    const T ms6 = m6 - P.s6 * (m6 + ruy) - P.hs6 * Fy;
+    const T ms7 = m7 - P.s7 * (m7 - (mul_rn(rux, ux) - mul_rn(ruy, uy))) +
+                  P.hs7 * (T(2) * (mul_rn(ux, Fx) - mul_rn(uy, Fy))) - P.s7 * (Qxx - Qyy);
+    const T ms8 = m8 - P.s8 * (m8 - rux * uy) + P.hs8 * (mul_rn(ux, Fy) + mul_rn(uy, Fx)) - P.s8 * Qxy;
 
-    // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-    const T a0 = rt * T(1.0 / 9.0), a1 = ms1 * T(1.0 / 36.0), a2 = ms2 * T(1.0 / 36.0);
+    // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+    // The rows of a1..a8 sum to zero over the nine outputs, so the mass of the
+    // node is 9 a0: a0 is rt/9 correctly rounded (one residual FMA), not
+    // rt * fl(1/9), whose constant is 7e-9 too large in FP32 and would add that
+    // bias to the mass at every step of a steady state.
+    const T c9 = T(1.0 / 9.0);
+    const T q9 = rt * c9;
+    const T a0 = fma(fma(-q9, T(9), rt), c9, q9);
+    const T a1 = ms1 * T(1.0 / 36.0), a2 = ms2 * T(1.0 / 36.0);
     const T a3 = ms3 * T(1.0 / 6.0), a4 = ms4 * T(1.0 / 12.0);
     const T a5 = ms5 * T(1.0 / 6.0), a6 = ms6 * T(1.0 / 12.0);
     const T a7 = ms7 * T(0.25), a8 = ms8 * T(0.25);
@@ -101,178 +167,250 @@ __device__ __forceinline__ void collide(const Phys<T>& P, const T (&f)[9], T Fx,
     out[8] = bdg + DX - DY - a8;
 }
 
-template <typename T, int BX, int BY, int NT>
-__global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, const int4* __restrict__ tiles,
-                                             int parity, unsigned long long timeout_ns) {
-    using Gm = Geom<T, BX, BY, NT>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar;
-    T* sf = reinterpret_cast<T*>(smem);
-    T* sp = reinterpret_cast<T*>(smem + Gm::psi_off);
-    const int tid = threadIdx.x;
+// Equation-of-state constants in registers.
+template <typename T, typename V> struct EosOf {
+    int eos;
+    V K, a, b, b4, RT, aalpha, two_over_G;
+    __device__ __forceinline__ explicit EosOf(const Phys<T>& P)
+        : eos(P.eos), K(P.K), a(P.a), b(P.b), b4(P.b4), RT(P.RT), aalpha(P.aalpha), two_over_G(P.two_over_G) {}
+};
+template <typename T> struct EosSel { using type = EosOf<T, const T&>; };
+template <> struct EosSel<float> { using type = EosOf<float, float>; };
+template <typename T> using EosRegs = typename EosSel<T>::type;
 
-    const int4 tile = tiles[blockIdx.x];
-    const Inst* I = insts + tile.x;
-    const int x0 = tile.y, y0 = tile.z;
-    const CUtensorMap* map = &I->tmap[parity];
+// Eq. 10 radicand with the pressure laws of lbm_internal.cuh, using Fast<T>.
+template <typename T> __device__ __forceinline__ T radicand_step(const EosRegs<T>& P, T rho) {
+    T p;
+    if (P.eos == LBM_EOS_CS) {
+        const T n = P.b4 * rho, q = T(1) - n;
+        const T num = T(1) + n * (T(1) + n * (T(1) - n));
+        p = P.K * (Fast<T>::div(rho * P.RT * num, q * q * q) - P.a * rho * rho);
+    } else if (P.eos == LBM_EOS_VDW) {
+        p = P.K * (Fast<T>::div(rho * P.RT, T(1) - P.b * rho) - P.a * rho * rho);
+    } else {
+        const T br = P.b * rho;
+        p = P.K * (Fast<T>::div(rho * P.RT, T(1) - br) -
+                   Fast<T>::div(P.aalpha * rho * rho, T(1) + T(2) * br - br * br));
+    }
+    return P.two_over_G * (p - rho * T(1.0 / 3.0));
+}
+
+// Persistent CTA over a strided list of tiles with a two-stage TMA pipeline:
+// while tile k is collided, the box of tile k+1 streams into the other
+// shared-memory buffer.
+template <typename T, int BX, int BY, int NT, int NBUF>
+__global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, const int4* __restrict__ tiles,
+                                             int ntiles, int parity, unsigned long long timeout_ns) {
+    using Gm = Geom<T, BX, BY, NT, NBUF>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x;
+    const int tx = tid % BX, ty = tid / BX;
+    int t = blockIdx.x;
+    if (t >= ntiles) return;
 
     if (tid == 0) {
-        acquire_tmap(map);
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>(Gm::box_bytes));
-        tma_load_3d(sf, map, x0 + Gm::GX - Gm::HX, y0, 0, &bar);
-    }
 
-    const Phys<T>& P = phys<T>(I);
-    const int nx = I->nx, ny = I->ny;
-    const unsigned flags = P.flags;
-
-    bool ok = mbar_wait_bounded(&bar, 0, timeout_ns);
-    if (flags & LBM_FLAG_TEST_FORCE_TIMEOUT) {
-        // parity 1 is the phase after the completed load: nothing completes it
-        ok = ok && mbar_wait_bounded(&bar, 1, 2000000ull);
-    }
-    if (!__syncthreads_and(ok)) {
-        if (tid == 0) {
-            atomicOr(I->status, ST_TIMEOUT);
-            mbar_wait_bounded(&bar, 0, timeout_ns);   // let a late copy land before exit
+    int last_inst = -1;   // thread 0 only: instance whose tensor map was last acquired
+    auto issue = [&](int tt, int bb) {
+        const int4 tl = tiles[tt];
+        const CUtensorMap* map = &insts[tl.x].tmap[parity];
+        if (tl.x != last_inst) {
+            acquire_tmap(map);
+            last_inst = tl.x;
         }
-        return;
-    }
+        mbar_arrive_expect_tx(&bar[bb], static_cast<uint32_t>(Gm::box_bytes));
+        tma_load_3d(smem + bb * Gm::buf_stride, map, tl.y + Gm::GX - Gm::HX, tl.z, 0, &bar[bb]);
+    };
+    if (tid == 0) issue(t, 0);
 
-    // ---- rho and psi of the tile and its ring (Eq. 10) -------------------
-    const int interact = P.interact;
-    const T rho_ref = P.rho_ref;
-    bool bad = false;
-    if (interact) {
-        for (int idx = tid; idx < Gm::WP * Gm::HP; idx += NT) {
-            const int i = idx % Gm::WP, j = idx / Gm::WP;
-            const T* q = sf + (j + 1) * Gm::WB + (i + Gm::HX - 1);
-            T r = T(0);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) r += q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
-            const T rad = psi_radicand(P, rho_ref + r);
-            sp[idx] = sqrt(rad);
-            const int x = x0 - 1 + i, y = y0 - 1 + j;
-            if (i >= 1 && i <= BX && j >= 1 && j <= BY && x < nx && y < ny && !(rad >= T(0))) bad = true;
-        }
-    }
-    __syncthreads();
-
-    // ---- collide and stream every owned node -----------------------------
-    const int tx = tid % BX, ty = tid / BX;
-    T* __restrict__ dst = static_cast<T*>(I->pop[parity ^ 1]);
-    const long long plane = I->plane;
-    const int pitch = I->pitch;
-    const T G = P.G, A = P.A;
-    const T hA = T(0.5) * A, omA = T(1) - A;
-    const T kG2 = P.kappa * G * T(0.5);
     constexpr T w1 = T(1.0 / 3.0), w2 = T(1.0 / 12.0);
+#pragma unroll 1
+    for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
+        const int b = NBUF == 2 ? (k & 1) : 0;
+        const uint32_t ph = NBUF == 2 ? ((k >> 1) & 1) : (k & 1);
+        const T* sf = reinterpret_cast<const T*>(smem + b * Gm::buf_stride);
+        T* sp = reinterpret_cast<T*>(smem + Gm::psi_off + b * Gm::psi_stride);
+        const int4 tile = tiles[t];
+        const Inst* I = insts + tile.x;
+        const int x0 = tile.y, y0 = tile.z;
+        const Phys<T>& P = phys<T>(I);
+        const int nx = I->nx, ny = I->ny;
+        const int interact = P.interact;
+        const EosRegs<T> E(P);
+        const Regs<T> R(P);
+        const T rho_ref = R.rho_ref;
+        bool bad = false;
+
+        bool ok = mbar_wait_bounded(&bar[b], ph, timeout_ns);
+        if (k == 0 && (P.flags & LBM_FLAG_TEST_FORCE_TIMEOUT)) {
+            // the phase after the completed first load: nothing completes it
+            ok = ok && mbar_wait_bounded(&bar[0], 1, 2000000ull);
+        }
+
+        // ---- rho and psi of the tile and its ring (Eq. 10) ---------------
+        if (interact && ok) {
+            auto ring = [&](int i, int j) {
+                const T* q = sf + (j + 1) * Gm::WB + (i + Gm::HX - 1);
+                T g[9];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) g[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
+                const T rad = radicand_step(E, rho_ref + rho_dev(g));
+                sp[j * Gm::WP + i] = Fast<T>::sqrt(rad);
+                if (!(rad >= T(0)) && i >= 1 && i <= BX && j >= 1 && j <= BY && x0 - 1 + i < nx &&
+                    y0 - 1 + j < ny)
+                    bad = true;
+            };
+            for (int j = ty; j < Gm::HP; j += Gm::TY) {
+                ring(tx, j);
+                if (tx < 2) ring(BX + tx, j);
+            }
+        }
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicOr(I->status, ST_TIMEOUT);
+                mbar_wait_bounded(&bar[b], ph, timeout_ns);   // let a late copy land before exit
+            }
+            return;
+        }
+        // every thread is past its reads of the other buffer: prefetch the next tile into it
+        if (NBUF == 2 && tid == 0 && t + static_cast<int>(gridDim.x) < ntiles) issue(t + gridDim.x, b ^ 1);
+
+        // ---- collide and stream every owned node -------------------------
+        T* __restrict__ dst = static_cast<T*>(I->pop[parity ^ 1]);
+        const long long plane = I->plane;
+        const int pitch = I->pitch;
+        const T G = P.G, A = P.A;
+        const T hA = T(0.5) * A, omA = T(1) - A;
+        const T kG2 = P.kappa * G * T(0.5);
+        const bool border = x0 < 2 || x0 + BX > nx - 2 || y0 < 2 || y0 + BY > ny - 2;
 
 #pragma unroll 1
-    for (int k = 0; k < Gm::ROWS; ++k) {
-        const int ly = ty + k * Gm::TY;
-        const int x = x0 + tx, y = y0 + ly;
-        if (x >= nx || y >= ny) continue;
-        const T* q = sf + (ly + GY) * Gm::WB + (tx + Gm::HX);
-        T f[9];
+        for (int r = 0; r < Gm::ROWS; ++r) {
+            const int ly = ty + r * Gm::TY;
+            const int x = x0 + tx, y = y0 + ly;
+            if (x >= nx || y >= ny) continue;
+            const T* q = sf + (ly + GY) * Gm::WB + (tx + Gm::HX);
+            T f[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) f[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
+            for (int a = 0; a < 9; ++a) f[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
 
-        T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
-        if (interact) {
-            const T* s = sp + (ly + 1) * Gm::WP + (tx + 1);
-            const T p0 = s[0];
-            const T p1 = s[1], p2 = s[Gm::WP], p3 = s[-1], p4 = s[-Gm::WP];
-            const T p5 = s[Gm::WP + 1], p6 = s[Gm::WP - 1], p7 = s[-Gm::WP - 1], p8 = s[-Gm::WP + 1];
-            const T q1 = p1 * p1, q2 = p2 * p2, q3 = p3 * p3, q4 = p4 * p4;
-            const T q5 = p5 * p5, q6 = p6 * p6, q7 = p7 * p7, q8 = p8 * p8;
-            // Eq. 9: F = -G [ (A/2) sum w psi_n^2 e + (1-A) psi sum w psi_n e ]
-            const T gx1 = w1 * (p1 - p3) + w2 * ((p5 - p7) + (p8 - p6));
-            const T gy1 = w1 * (p2 - p4) + w2 * ((p5 - p7) + (p6 - p8));
-            const T gx2 = w1 * (q1 - q3) + w2 * ((q5 - q7) + (q8 - q6));
-            const T gy2 = w1 * (q2 - q4) + w2 * ((q5 - q7) + (q6 - q8));
-            Fx = -G * (hA * gx2 + omA * p0 * gx1);
-            Fy = -G * (hA * gy2 + omA * p0 * gy1);
-            // Eq. 23 (x G/2): sums of w (psi_n - psi) e e and w (psi_n^2 - psi^2) e e;
-            // sum w e_x^2 = sum w e_y^2 = 1 and sum w e_x e_y = 0 over the ring
-            const T d1 = w2 * ((p5 + p7) + (p6 + p8));
-            const T d2 = w2 * ((q5 + q7) + (q6 + q8));
-            const T q0 = p0 * p0;
-            const T sxx1 = w1 * (p1 + p3) + d1 - p0, syy1 = w1 * (p2 + p4) + d1 - p0;
-            const T sxy1 = w2 * ((p5 + p7) - (p6 + p8));
-            const T sxx2 = w1 * (q1 + q3) + d2 - q0, syy2 = w1 * (q2 + q4) + d2 - q0;
-            const T sxy2 = w2 * ((q5 + q7) - (q6 + q8));
-            const T c = omA * p0;
-            Qxx = kG2 * (c * sxx1 + hA * sxx2);
-            Qyy = kG2 * (c * syy1 + hA * syy2);
-            Qxy = kG2 * (c * sxy1 + hA * sxy2);
-        }
+            T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
+            if (interact) {
+                const T* s = sp + (ly + 1) * Gm::WP + (tx + 1);
+                const T p0 = s[0];
+                const T p1 = s[1], p2 = s[Gm::WP], p3 = s[-1], p4 = s[-Gm::WP];
+                const T p5 = s[Gm::WP + 1], p6 = s[Gm::WP - 1], p7 = s[-Gm::WP - 1], p8 = s[-Gm::WP + 1];
+                const T q1 = mul_rn(p1, p1), q2 = mul_rn(p2, p2), q3 = mul_rn(p3, p3), q4 = mul_rn(p4, p4);
+                const T q5 = mul_rn(p5, p5), q6 = mul_rn(p6, p6), q7 = mul_rn(p7, p7), q8 = mul_rn(p8, p8);
+                // Eq. 9: F = -G [ (A/2) sum w psi_n^2 e + (1-A) psi sum w psi_n e ]
+                const T gx1 = w1 * (p1 - p3) + w2 * ((p5 - p7) + (p8 - p6));
+                const T gy1 = w1 * (p2 - p4) + w2 * ((p5 - p7) + (p6 - p8));
+                const T gx2 = w1 * (q1 - q3) + w2 * ((q5 - q7) + (q8 - q6));
+                const T gy2 = w1 * (q2 - q4) + w2 * ((q5 - q7) + (q6 - q8));
+                Fx = -G * (hA * gx2 + omA * p0 * gx1);
+                Fy = -G * (hA * gy2 + omA * p0 * gy1);
+                // Eq. 23 (x G/2): sums of w (psi_n - psi) e e and w (psi_n^2 - psi^2) e e;
+                // sum w e_x^2 = sum w e_y^2 = 1 and sum w e_x e_y = 0 over the ring
+                const T d1 = w2 * ((p5 + p7) + (p6 + p8));
+                const T d2 = w2 * ((q5 + q7) + (q6 + q8));
+                const T q0 = mul_rn(p0, p0);
+                const T sxx1 = w1 * (p1 + p3) + d1 - p0, syy1 = w1 * (p2 + p4) + d1 - p0;
+                const T sxy1 = w2 * ((p5 + p7) - (p6 + p8));
+                const T sxx2 = w1 * (q1 + q3) + d2 - q0, syy2 = w1 * (q2 + q4) + d2 - q0;
+                const T sxy2 = w2 * ((q5 + q7) - (q6 + q8));
+                const T c = omA * p0;
+                Qxx = kG2 * (c * sxx1 + hA * sxx2);
+                Qyy = kG2 * (c * syy1 + hA * syy2);
+                Qxy = kG2 * (c * sxy1 + hA * sxy2);
+            }
 
-        T out[9];
-        collide(P, f, Fx, Fy, Qxx, Qyy, Qxy, out);
-        if (!(out[0] == out[0])) bad = true;
+            T out[9];
+            collide(R, f, Fx, Fy, Qxx, Qyy, Qxy, out);
+            if (!(out[0] == out[0])) bad = true;
 
-        T* o = dst + static_cast<long long>(y + GY) * pitch + (x + Gm::GX);
+            T* o = dst + static_cast<long long>(y + GY) * pitch + (x + Gm::GX);
 #pragma unroll
-        for (int a = 0; a < 9; ++a) o[a * plane] = out[a];
+            for (int a = 0; a < 9; ++a) o[a * plane] = out[a];
 
-        // periodic images in the ghost cells read by the neighbouring tiles
-        const bool xl = x < 2, xr = x >= nx - 2, yl = y < 2, yr = y >= ny - 2;
-        if (xl || xr || yl || yr) {
-            const int oxs[3] = {0, xl ? nx : 0, xr ? -nx : 0};
-            const int oys[3] = {0, yl ? ny : 0, yr ? -ny : 0};
-            const bool hx[3] = {true, xl, xr};
-            const bool hy[3] = {true, yl, yr};
-            for (int iy = 0; iy < 3; ++iy)
-                for (int ix = 0; ix < 3; ++ix) {
-                    if (!(hx[ix] && hy[iy]) || (ix == 0 && iy == 0)) continue;
-                    T* g = o + static_cast<long long>(oys[iy]) * pitch + oxs[ix];
+            // periodic images in the ghost cells read by the neighbouring tiles
+            if (border) {
+                const bool xl = x < 2, xr = x >= nx - 2, yl = y < 2, yr = y >= ny - 2;
+                if (xl || xr || yl || yr) {
+                    const int oxs[3] = {0, xl ? nx : 0, xr ? -nx : 0};
+                    const int oys[3] = {0, yl ? ny : 0, yr ? -ny : 0};
+                    const bool hx[3] = {true, xl, xr};
+                    const bool hy[3] = {true, yl, yr};
+                    for (int iy = 0; iy < 3; ++iy)
+                        for (int ix = 0; ix < 3; ++ix) {
+                            if (!(hx[ix] && hy[iy]) || (ix == 0 && iy == 0)) continue;
+                            T* g = o + static_cast<long long>(oys[iy]) * pitch + oxs[ix];
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) g[a * plane] = out[a];
+                            for (int a = 0; a < 9; ++a) g[a * plane] = out[a];
+                        }
                 }
+            }
         }
+        if (bad) atomicOr(I->status, ST_UNSTABLE);
     }
-    if (bad) atomicOr(I->status, ST_UNSTABLE);
 }
 
 // ---- tile configurations ------------------------------------------------
-template <typename T, int BX, int BY, int NT> struct Cfg {
-    using Gm = Geom<T, BX, BY, NT>;
-    static TileCfg tc() { return TileCfg{BX, BY, NT}; }
+template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
+    using Gm = Geom<T, BX, BY, NT, NBUF>;
+    static int grid_cap;   // resident CTAs on the device (persistent grid)
+    static TileCfg tc() { return TileCfg{BX, BY, NT, NBUF}; }
     static size_t smem() { return Gm::smem; }
     static cudaError_t prepare() {
-        return cudaFuncSetAttribute(k_step<T, BX, BY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(Gm::smem));
+        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, NT, NBUF>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(Gm::smem));
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<T, BX, BY, NT, NBUF>, NT, Gm::smem)) !=
+            cudaSuccess)
+            return e;
+        grid_cap = (occ > 0 ? occ : 1) * sms;
+        return cudaSuccess;
     }
     static cudaError_t launch(const Inst* d, const int4* t, int n, int parity, unsigned long long to,
                               cudaStream_t st) {
-        k_step<T, BX, BY, NT><<<n, NT, Gm::smem, st>>>(d, t, parity, to);
+        // one CTA per tile, or a persistent grid of resident CTAs striding over the tiles
+        const int grid = NBUF == 1 ? n : (n < grid_cap ? n : grid_cap);
+        k_step<T, BX, BY, NT, NBUF><<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to);
         return cudaGetLastError();
     }
 };
+template <typename T, int BX, int BY, int NT, int NBUF> int Cfg<T, BX, BY, NT, NBUF>::grid_cap = 1;
 
 struct Entry {
     TileCfg (*tc)();
     size_t (*smem)();
     cudaError_t (*prepare)();
     cudaError_t (*launch)(const Inst*, const int4*, int, int, unsigned long long, cudaStream_t);
+    int nbuf;
 };
 
-#define LBM_CFG(T, BX, BY, NT) \
-    Entry { &Cfg<T, BX, BY, NT>::tc, &Cfg<T, BX, BY, NT>::smem, &Cfg<T, BX, BY, NT>::prepare, &Cfg<T, BX, BY, NT>::launch }
+#define LBM_CFG(T, BX, BY, NT, NB)                                                                    \
+    Entry {                                                                                          \
+        &Cfg<T, BX, BY, NT, NB>::tc, &Cfg<T, BX, BY, NT, NB>::smem, &Cfg<T, BX, BY, NT, NB>::prepare, \
+            &Cfg<T, BX, BY, NT, NB>::launch, NB                                                      \
+    }
 
 const Entry kF32[] = {
-    LBM_CFG(float, 64, 16, 256), LBM_CFG(float, 32, 16, 256), LBM_CFG(float, 64, 8, 256),
-    LBM_CFG(float, 128, 8, 256), LBM_CFG(float, 128, 16, 512), LBM_CFG(float, 32, 32, 256),
+    LBM_CFG(float, 128, 16, 512, 1), LBM_CFG(float, 64, 16, 256, 1), LBM_CFG(float, 128, 8, 256, 1),
+    LBM_CFG(float, 64, 32, 512, 1),  LBM_CFG(float, 32, 32, 256, 1), LBM_CFG(float, 64, 16, 256, 2),
+    LBM_CFG(float, 64, 8, 256, 2),   LBM_CFG(float, 32, 16, 256, 2),
 };
 const Entry kF64[] = {
-    LBM_CFG(double, 32, 8, 256), LBM_CFG(double, 64, 8, 256), LBM_CFG(double, 32, 16, 256),
-    LBM_CFG(double, 64, 4, 256),
+    LBM_CFG(double, 32, 8, 256, 1),  LBM_CFG(double, 64, 8, 256, 1), LBM_CFG(double, 32, 16, 256, 1),
+    LBM_CFG(double, 64, 4, 256, 1),  LBM_CFG(double, 32, 8, 256, 2),
 };
 
 const Entry* table(int prec, int* n) {

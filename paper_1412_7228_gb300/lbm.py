@@ -118,7 +118,7 @@ def lib():
         "lbm_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
         "lbm_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
         "lbm_tile_config_count": ([ctypes.c_int], ctypes.c_int),
-        "lbm_tile_config": ([ctypes.c_int, ctypes.c_int, _ip, _ip, _ip], ctypes.c_int),
+        "lbm_tile_config": ([ctypes.c_int, ctypes.c_int, _ip, _ip, _ip, _ip], ctypes.c_int),
         "lbm_set_schedule": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "lbm_autotune": ([_vp, ctypes.c_int, _ip, _ip, _dp], ctypes.c_int),
         "lbm_use_graphs": ([_vp, ctypes.c_int], ctypes.c_int),
@@ -198,11 +198,12 @@ def lbm_batch_required_bytes(nx: Sequence[int], ny: Sequence[int], precision: in
 
 
 def lbm_tile_configs(precision: int):
+    """(tile width, tile height, threads per CTA, pipeline stages) per configuration."""
     out = []
     for k in range(lib().lbm_tile_config_count(precision)):
-        bx, by, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        lib().lbm_tile_config(precision, k, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(nt))
-        out.append((bx.value, by.value, nt.value))
+        bx, by, nt, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib().lbm_tile_config(precision, k, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(nt), ctypes.byref(st))
+        out.append((bx.value, by.value, nt.value, st.value))
     return out
 
 

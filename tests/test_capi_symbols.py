@@ -42,7 +42,7 @@ def test_host_only_calls_work_without_a_gpu(liblbm):
     assert liblbm.lbm_bytes_per_update(P.LBM_FP32) == 72
     assert liblbm.lbm_bytes_per_update(P.LBM_FP64) == 144
     cfgs = P.lbm_tile_configs(P.LBM_FP32)
-    assert (64, 16, 256) in cfgs
+    assert (128, 16, 512, 1) in cfgs and all(c[3] in (1, 2) for c in cfgs)
 
 
 def test_product_eos_helpers_agree_with_the_oracle():

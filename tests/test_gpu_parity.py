@@ -288,3 +288,23 @@ def test_bounded_wait_reports_timeout_and_context_survives(P):
     ref = oracle_run(op, rho0, 10)
     assert rel(lat.read_populations(), ref) <= 2e-5
     lat.close()
+
+
+def test_symmetric_droplet_stays_bitwise_mirror_symmetric(P):
+    """Rounding of the FP32 path respects the lattice mirrors: a centred drop
+    stays symmetric to the last bit, so it cannot drift off its centre."""
+    eos, op, rg, rl = cs_case(P, kappa=0.3)
+    n = 64
+    rho0 = I.droplet_density(n, n, 15, rl, rg)
+    lat = P.Lattice(n, n, P.LBM_FP32)
+    lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+    lat.init_density(rho0)
+    lat.step(2000)
+    f = lat.read_populations()
+    lat.close()
+    mx = [0, 3, 2, 1, 4, 6, 5, 8, 7]          # x -> -x
+    my = [0, 1, 4, 3, 2, 8, 7, 6, 5]          # y -> -y
+    xs = (-np.arange(n)) % n
+    for a in range(9):
+        assert np.array_equal(f[a], f[mx[a]][:, xs]), a
+        assert np.array_equal(f[a], f[my[a]][xs, :]), a
