@@ -210,6 +210,32 @@ int lbm_bytes_per_update(int precision);
 
 const char* lbm_last_error(lbm_ctx* ctx);
 
+/* ---- Allocation-free Laplace sampling of a device density field ----------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: one whose device memory is all owned by
+ * another allocator (a framework's caching allocator or a fixed arena), or a
+ * latency-critical loop that must not make an allocation call, which can
+ * synchronise the whole device.
+ *
+ * Same sums as lbm_batch_measure (Eq. 22 sampling, FP64), but over a density
+ * field d_rho of nx*ny doubles (row-major, x fastest) that the caller keeps in
+ * device memory; out receives LBM_MEASURE_N doubles in host memory {p_in,
+ * p_out, rho_in, rho_out, R_eq, mass, n_in, n_out}, with p = p_EOS(rho) of eos.
+ * Work runs on `stream` (NULL: legacy default stream), which the call
+ * synchronises before it returns.
+ *
+ * It allocates nothing: its scratch is a file-scope device array sized for at
+ * most LBM_STATIC_MAX_NODES nodes (about 128 KiB, held by every GPU that loads
+ * the library until the process exits).  Larger fields are rejected with
+ * LBM_EINVAL before any GPU work.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race.
+ * Returns LBM_OK, LBM_EINVAL or LBM_ECUDA. */
+#define LBM_STATIC_MAX_NODES 16777216
+int lbm_field_pressure_jump_static(const double* d_rho, int nx, int ny, const lbm_eos* eos, double cx,
+                                   double cy, double r_in, double r_out, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,7 +37,7 @@ EXPORTS = [
     "lbm_measure_pressure_jump", "lbm_batch_measure", "lbm_stats", "lbm_batch_stats",
     "lbm_save", "lbm_load", "lbm_tile_config_count", "lbm_tile_config", "lbm_set_schedule",
     "lbm_autotune", "lbm_use_graphs", "lbm_steps_done", "lbm_kernel_launches", "lbm_bytes_per_update",
-    "lbm_last_error",
+    "lbm_last_error", "lbm_field_pressure_jump_static",
 ]
 
 
@@ -126,6 +126,8 @@ def lib():
         "lbm_kernel_launches": ([_vp], ctypes.c_longlong),
         "lbm_bytes_per_update": ([ctypes.c_int], ctypes.c_int),
         "lbm_last_error": ([_vp], ctypes.c_char_p),
+        "lbm_field_pressure_jump_static": ([_vp, ctypes.c_int, ctypes.c_int, E, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, _dp, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -184,6 +186,21 @@ def lbm_laplace_fit(dp: Sequence[float], R: Sequence[float]):
     _check(None, lib().lbm_laplace_fit(len(dp), _ptr(dp), _ptr(R), ctypes.byref(s), ctypes.byref(c),
                                        ctypes.byref(r2)))
     return s.value, c.value, r2.value
+
+
+LBM_STATIC_MAX_NODES = 16777216
+
+
+def lbm_field_pressure_jump_static(d_rho_ptr: int, nx: int, ny: int, eos: Eos, cx: float, cy: float,
+                                   r_in: float, r_out: float, stream_ptr: int = 0) -> dict:
+    """Allocation-free Laplace sampling of a density field already in device
+    memory (``d_rho_ptr``: device address of nx*ny doubles).  For callers that
+    cannot allocate device memory; see include/lbm.h for the scratch rules."""
+    o = np.empty(LBM_MEASURE_N)
+    _check(None, lib().lbm_field_pressure_jump_static(ctypes.c_void_p(d_rho_ptr), nx, ny, ctypes.byref(eos.c()),
+                                                      cx, cy, r_in, r_out, _ptr(o), ctypes.c_void_p(stream_ptr)))
+    keys = ("p_in", "p_out", "rho_in", "rho_out", "R_eq", "mass", "n_in", "n_out")
+    return dict(zip(keys, (float(v) for v in o)))
 
 
 def lbm_required_bytes(nx: int, ny: int, precision: int) -> int:
