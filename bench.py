@@ -72,7 +72,7 @@ def kernel_traffic(prec_name):
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "step_%s_4096_traffic.txt" % prec_name)
     try:
-        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line)
+        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
     except OSError:
         return None
     if kv.get("lbm_step_cu_sha256_16") != sha:
@@ -81,6 +81,27 @@ def kernel_traffic(prec_name):
         return float(kv["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def fp64_alu_roofline(mlups):
+    """FP64 step against the FP64 pipe: GB300 issues 2 FP64 thread-operations
+    per clock per SM; the kernel's FP64 operations per lattice update come
+    from the committed ncu summary (valid while the kernel is unchanged)."""
+    src = os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", "lbm_step.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "step_fp64_1024_alu.txt")
+    try:
+        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
+        if kv.get("lbm_step_cu_sha256_16") != sha:
+            return None
+        ops = float(kv["fp64_ops_per_update"])
+    except (OSError, KeyError, ValueError):
+        return None
+    sm_mhz, sms = 2070.0, 152
+    peak = 2.0 * sms * sm_mhz * 1e6 / 1e9          # G FP64 thread-operations per second
+    achieved = ops * mlups * 1e6 / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP64 ops/s", "frac": achieved / peak,
+            "ops_per_update": ops, "peak_from": "2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz"}
 
 
 class ClockSampler:
@@ -275,15 +296,20 @@ def run_ours(args):
     fp64 = None
     if not args.no_fp64 and prec == P.LBM_FP32:
         lat64 = make_lattice(P, nx, ny, P.LBM_FP64, rho0)
+        lat64.set_schedule(1, 0)
         lat64.use_graphs(True)
         lat64.step(min(args.warmup, 10))
         lat64.sync()
-        k64 = max(32, args.steps // 8)
+        k64 = max(32, args.steps // 32)
         t64 = time_steps(torch, lat64, k64)
         lat64.sync()
         m64 = N * k64 / t64 / 1e6
         fp64 = {"value": m64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1000.0,
-                "hbm_frac": 144 * N / (t64 / k64) / 1e9 / peak, "bytes_per_update": 144}
+                "hbm_frac": 144 * N / (t64 / k64) / 1e9 / peak, "bytes_per_update": 144,
+                "kernel": "lbm::k_step<double,%d,%d,%d,%d>" % tuple(P.lbm_tile_configs(P.LBM_FP64)[1])}
+        alu = fp64_alu_roofline(m64)
+        if alu:
+            fp64["roofline"] = alu
         lat64.close()
 
     # ---- end to end through the public API with host buffers -------------
