@@ -210,6 +210,54 @@ int lbm_bytes_per_update(int precision);
 
 const char* lbm_last_error(lbm_ctx* ctx);
 
+/* ---- Learned surrogate: MLP 3 -> 64 -> 64 -> 4 --------------------------
+ * Maps (T/Tc, A, kappa) to (sigma, rho_l, rho_g, peak spurious velocity),
+ * trained on droplet simulations of this library; its inverse picks the
+ * kappa of Eq. 23 that gives a requested sigma.  Not in the paper.
+ * GELU (exact, 0.5 z (1 + erf(z / sqrt 2))) after both hidden layers, FP32
+ * weights and FP32 accumulation, mean-squared error on standardised targets,
+ * Adam.  Parameters are one flat FP32 array of LBM_MLP_NPARAMS entries:
+ * W1[64][3], b1[64], W2[64][64], b2[64], W3[4][64], b3[4] (row-major,
+ * y = W x + b).  Inputs and targets are standardised inside with the
+ * normalisation set by lbm_mlp_set_normalization (mean and std per column).
+ * All host arrays are row-major FP32 (n x 3 inputs, n x 4 targets). */
+#define LBM_MLP_IN 3
+#define LBM_MLP_HIDDEN 64
+#define LBM_MLP_OUT 4
+#define LBM_MLP_NPARAMS 4676
+
+typedef struct lbm_mlp lbm_mlp;
+
+/* Create a network with seeded uniform(+-sqrt(6/(fan_in+fan_out))) weights and
+ * zero biases on the given stream (NULL: legacy default); allocates its own
+ * device buffers for up to max_samples training samples. */
+int lbm_mlp_create(lbm_mlp** out, int max_samples, unsigned long long seed, void* stream);
+void lbm_mlp_destroy(lbm_mlp* m);
+int lbm_mlp_set_normalization(lbm_mlp* m, const float in_mean[3], const float in_std[3], const float out_mean[4],
+                              const float out_std[4]);
+int lbm_mlp_set_params(lbm_mlp* m, const float* params);
+int lbm_mlp_get_params(lbm_mlp* m, float* params);
+/* Mean-squared-error loss over n samples (standardised targets, mean over
+ * samples and outputs) and its gradient with respect to every parameter,
+ * computed by the training kernels without an update (gradient checks). */
+int lbm_mlp_loss_grad(lbm_mlp* m, const float* X, const float* Y, int n, float* loss, float* grad);
+/* One Adam step (lr, beta1, beta2, eps) on the full batch of n samples. */
+int lbm_mlp_adam_step(lbm_mlp* m, const float* X, const float* Y, int n, float lr, float beta1, float beta2,
+                      float eps);
+/* Train for `epochs` passes over n samples in shuffled minibatches of
+ * `batch` (seeded), Adam(lr, 0.9, 0.999, 1e-8); loss_per_epoch (nullable)
+ * receives the mean minibatch loss of each epoch. */
+int lbm_mlp_train(lbm_mlp* m, const float* X, const float* Y, int n, int epochs, int batch, float lr,
+                  unsigned long long seed, float* loss_per_epoch);
+/* Forward pass: n raw inputs -> n raw outputs (de-standardised). */
+int lbm_mlp_predict(lbm_mlp* m, const float* X, int n, float* Y);
+/* Inverse: for each of m targets (t_over_tc[i], A[i], sigma[i]) the kappa in
+ * [kappa_lo, kappa_hi] whose predicted sigma equals sigma[i] (bisection on
+ * the GPU; predicted sigma must decrease in kappa, as Eq. 28 has it).  NaN
+ * where the target lies outside the predicted range. */
+int lbm_mlp_invert_kappa(lbm_mlp* m, const float* t_over_tc, const float* A, const float* sigma, int count,
+                         float kappa_lo, float kappa_hi, float* kappa_out);
+
 /* ---- Allocation-free Laplace sampling of a device density field ----------
  * The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory: one whose device memory is all owned by

@@ -38,6 +38,8 @@ EXPORTS = [
     "lbm_save", "lbm_load", "lbm_tile_config_count", "lbm_tile_config", "lbm_set_schedule",
     "lbm_autotune", "lbm_use_graphs", "lbm_steps_done", "lbm_kernel_launches", "lbm_bytes_per_update",
     "lbm_last_error", "lbm_field_pressure_jump_static",
+    "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_set_normalization", "lbm_mlp_set_params", "lbm_mlp_get_params",
+    "lbm_mlp_loss_grad", "lbm_mlp_adam_step", "lbm_mlp_train", "lbm_mlp_predict", "lbm_mlp_invert_kappa",
 ]
 
 
@@ -70,6 +72,7 @@ class Eos:
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 _ip = ctypes.POINTER(ctypes.c_int)
 _vp = ctypes.c_void_p
 
@@ -128,6 +131,19 @@ def lib():
         "lbm_last_error": ([_vp], ctypes.c_char_p),
         "lbm_field_pressure_jump_static": ([_vp, ctypes.c_int, ctypes.c_int, E, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _dp, _vp], ctypes.c_int),
+        "lbm_mlp_create": ([ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_ulonglong, _vp], ctypes.c_int),
+        "lbm_mlp_destroy": ([_vp], None),
+        "lbm_mlp_set_normalization": ([_vp, _fp, _fp, _fp, _fp], ctypes.c_int),
+        "lbm_mlp_set_params": ([_vp, _fp], ctypes.c_int),
+        "lbm_mlp_get_params": ([_vp, _fp], ctypes.c_int),
+        "lbm_mlp_loss_grad": ([_vp, _fp, _fp, ctypes.c_int, _fp, _fp], ctypes.c_int),
+        "lbm_mlp_adam_step": ([_vp, _fp, _fp, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float], ctypes.c_int),
+        "lbm_mlp_train": ([_vp, _fp, _fp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                           ctypes.c_ulonglong, _fp], ctypes.c_int),
+        "lbm_mlp_predict": ([_vp, _fp, ctypes.c_int, _fp], ctypes.c_int),
+        "lbm_mlp_invert_kappa": ([_vp, _fp, _fp, _fp, ctypes.c_int, ctypes.c_float, ctypes.c_float, _fp],
+                                 ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -365,3 +381,95 @@ class Lattice(Batch):
 
     def measure_pressure_jump(self, cx: float, cy: float, r_in: float, r_out: float) -> dict:
         return self.measure(0, cx, cy, r_in, r_out)
+
+
+# ---- learned surrogate --------------------------------------------------
+MLP_NPARAMS = 4676
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _fptr(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_fp)
+
+
+class Mlp:
+    """The 3-64-64-4 GELU surrogate (lbm_mlp_*): training and inference run
+    in the library's CUDA kernels; this class only marshals arrays."""
+
+    def __init__(self, max_samples: int = 4096, seed: int = 0, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.h = ctypes.c_void_p()
+        _check(None, lib().lbm_mlp_create(ctypes.byref(self.h), int(max_samples), int(seed),
+                                          ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().lbm_mlp_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_normalization(self, in_mean, in_std, out_mean, out_std):
+        a = [_f32(v) for v in (in_mean, in_std, out_mean, out_std)]
+        _check(None, lib().lbm_mlp_set_normalization(self.h, *[_fptr(v) for v in a]))
+
+    def fit_normalization(self, X, Y):
+        X = np.asarray(X, dtype=np.float64)
+        Y = np.asarray(Y, dtype=np.float64)
+        self.set_normalization(X.mean(0), X.std(0) + 1e-12, Y.mean(0), Y.std(0) + 1e-12)
+
+    def set_params(self, p):
+        p = _f32(p, (MLP_NPARAMS,))
+        _check(None, lib().lbm_mlp_set_params(self.h, _fptr(p)))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(MLP_NPARAMS, dtype=np.float32)
+        _check(None, lib().lbm_mlp_get_params(self.h, _fptr(p)))
+        return p
+
+    def loss_grad(self, X, Y):
+        X = _f32(X)
+        Y = _f32(Y)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.empty(MLP_NPARAMS, dtype=np.float32)
+        _check(None, lib().lbm_mlp_loss_grad(self.h, _fptr(X), _fptr(Y), len(X), _fptr(loss), _fptr(g)))
+        return float(loss[0]), g
+
+    def adam_step(self, X, Y, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        X = _f32(X)
+        Y = _f32(Y)
+        _check(None, lib().lbm_mlp_adam_step(self.h, _fptr(X), _fptr(Y), len(X), lr, beta1, beta2, eps))
+
+    def train(self, X, Y, epochs=200, batch=128, lr=1e-3, seed=0):
+        X = _f32(X)
+        Y = _f32(Y)
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(None, lib().lbm_mlp_train(self.h, _fptr(X), _fptr(Y), len(X), epochs, batch, lr, seed,
+                                         _fptr(losses)))
+        return losses
+
+    def predict(self, X) -> np.ndarray:
+        X = _f32(X)
+        Y = np.empty((len(X), 4), dtype=np.float32)
+        _check(None, lib().lbm_mlp_predict(self.h, _fptr(X), len(X), _fptr(Y)))
+        return Y
+
+    def invert_kappa(self, t_over_tc, A, sigma, lo=0.0, hi=0.6) -> np.ndarray:
+        t = _f32(t_over_tc)
+        a = _f32(A)
+        s = _f32(sigma)
+        k = np.empty(len(t), dtype=np.float32)
+        _check(None, lib().lbm_mlp_invert_kappa(self.h, _fptr(t), _fptr(a), _fptr(s), len(t), lo, hi, _fptr(k)))
+        return k

@@ -1,0 +1,32 @@
+"""The learned surrogate end to end at a small scale (64x64 droplets): data
+from batched simulations, training on the GPU, kappa picks by the GPU
+inverse, every pick re-simulated.  It also shows what the network gains over
+choosing kappa without it (Eq. 28's sigma = (1 - kappa) sigma(0) from one
+simulation at kappa = 0): no simulation is needed to pick, and the picks land
+closer to the requested sigma because the network learned the curvature of
+sigma(kappa) that the leading-order rule leaves out."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_7228_gb300 import surrogate
+    return surrogate
+
+
+def test_pipeline_small(S):
+    rep = S.pipeline(n=384, L_=64, steps=3000, epochs=300, n_req=8, seed=3)
+    assert rep["stable"] >= 0.9 * rep["samples"]
+    first, last = rep["train_loss_first_last"]
+    assert last < 0.05 * first
+    assert len(rep["targets"]) >= 4 and all(np.isfinite(rep["kappa"]))
+    err = np.abs(rep["resim_rel_err"])
+    lin = np.abs(rep["linear_rule_rel_err"])
+    assert err.max() < 0.05
+    assert err.mean() < lin.mean()
