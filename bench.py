@@ -55,6 +55,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest of every rank's value (the timed region ends when the
+    slowest replica ends); the identity on one rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, nodes_per_rank, steps, seconds):
+    """Lattice updates of all replicas per second, in millions (weak scaling:
+    each rank owns one full lattice)."""
+    return world * nodes_per_rank * steps / seconds / 1e6
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -277,11 +294,8 @@ def run_ours(args):
         lat.sync()
     except P.LbmError:
         status_ok = False
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    mlups = ws * N * args.steps / t / 1e6
+    t = max_over_ranks(t, dist, "cuda")
+    mlups = whole_job_mlups(ws, N, args.steps, t)
     avg_launch = t / args.steps
     peak, peak_kind = measured_peak()
     bpu = 72 if prec == P.LBM_FP32 else 144

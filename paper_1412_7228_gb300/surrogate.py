@@ -87,15 +87,19 @@ def predict(mlp: L.Mlp, X: np.ndarray) -> np.ndarray:
     return from_net(mlp.predict(X))
 
 
-def requests(Y_ok: np.ndarray, X_ok: np.ndarray, n: int = 16) -> Tuple[float, float, np.ndarray]:
-    """n sigma targets over the 5-95 % range of the data's sigma, at the
-    data's median (T/Tc, A)."""
+def requests(mlp: L.Mlp, Y_ok: np.ndarray, X_ok: np.ndarray, n: int = 16, k_lo: float = 0.0, k_hi: float = 0.6
+             ) -> Tuple[float, float, np.ndarray]:
+    """n sigma targets spread evenly over the part of the data's 5-95 %
+    sigma range that kappa in [k_lo, k_hi] can reach at the data's median
+    (T/Tc, A) (1 % inside its ends)."""
     tr, A = float(np.median(X_ok[:, 0])), float(np.median(X_ok[:, 1]))
     lo, hi = np.percentile(Y_ok[:, 0], [5, 95])
+    s_hi, s_lo = predict(mlp, np.array([[tr, A, k_lo], [tr, A, k_hi]]))[:, 0]
+    lo, hi = max(lo, s_lo * 1.01), min(hi, s_hi * 0.99)
     return tr, A, np.linspace(lo, hi, n)
 
 
-def pipeline(n: int = 2000, L_: int = 256, steps: int = 20000, epochs: int = 600, n_req: int = 16,
+def pipeline(n: int = 2000, L_: int = 256, steps: int = 40000, epochs: int = 600, n_req: int = 16,
              seed: int = 1, save: str = None) -> Dict:
     X = sample_params(n, seed)
     t0 = time.perf_counter()
@@ -105,10 +109,7 @@ def pipeline(n: int = 2000, L_: int = 256, steps: int = 20000, epochs: int = 600
         np.savez(save, X=X, Y=Y, ok=ok)
     Xo, Yo = X[ok], Y[ok]
     mlp, losses = train(Xo, Yo, epochs=epochs)
-    tr, A, targets = requests(Yo, Xo, n_req)
-    # keep only targets reachable with kappa in [0, 0.6] at this (T, A)
-    edge = predict(mlp, np.array([[tr, A, 0.0], [tr, A, 0.6]]))[:, 0]
-    targets = targets[(targets <= edge[0]) & (targets >= edge[1])]
+    tr, A, targets = requests(mlp, Yo, Xo, n_req)
     t1 = time.perf_counter()
     # output 0 is log sigma, which decreases in kappa as sigma does
     kappa = mlp.invert_kappa(np.full(len(targets), tr), np.full(len(targets), A), np.log(targets), 0.0, 0.6)
@@ -143,7 +144,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="train the sigma surrogate and check its kappa picks")
     ap.add_argument("--n", type=int, default=2000)
     ap.add_argument("--L", type=int, default=256)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=40000,
+                    help="steps per droplet; a 256^2 drop with R0 = 51 settles by 30-40k steps")
     ap.add_argument("--epochs", type=int, default=600)
     ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--save", default=None, help="write the data set (X, Y, ok) to this .npz")

@@ -25,7 +25,7 @@ def test_pipeline_small(S):
     assert rep["stable"] >= 0.9 * rep["samples"]
     first, last = rep["train_loss_first_last"]
     assert last < 0.05 * first
-    assert len(rep["targets"]) >= 4 and all(np.isfinite(rep["kappa"]))
+    assert len(rep["targets"]) == 8 and all(np.isfinite(rep["kappa"]))
     err = np.abs(rep["resim_rel_err"])
     lin = np.abs(rep["linear_rule_rel_err"])
     assert err.max() < 0.05
