@@ -211,6 +211,8 @@ struct lbm_ctx {
     int cfg = 0, sched = 0;
     bool use_graphs = false;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    lbm::StepArgs<float> one_f{};    // kernel argument block of a one-lattice context
+    lbm::StepArgs<double> one_d{};
     std::string err;
 };
 
@@ -274,6 +276,34 @@ int upload_insts(lbm_ctx* c) {
     return LBM_OK;
 }
 
+// A context of one lattice passes its descriptor by value (kernel argument
+// block); refreshed whenever the tensor maps or the parameters change.
+template <typename T> void fill_one(lbm_ctx* c, lbm::StepArgs<T>& a, const lbm::Phys<T>& P) {
+    const Inst& I = c->h[0];
+    a.tmap[0] = I.tmap[0];
+    a.tmap[1] = I.tmap[1];
+    a.P = P;
+    a.pop[0] = I.pop[0];
+    a.pop[1] = I.pop[1];
+    a.status = I.status;
+    a.plane = I.plane;
+    a.nx = I.nx;
+    a.ny = I.ny;
+    a.pitch = I.pitch;
+    a.tiles_x = (I.nx + lbm::step_config(c->prec, c->cfg).bx - 1) / lbm::step_config(c->prec, c->cfg).bx;
+}
+
+void refresh_one(lbm_ctx* c) {
+    if (c->n != 1) return;
+    fill_one(c, c->one_f, c->h[0].pf);
+    fill_one(c, c->one_d, c->h[0].pd);
+}
+
+const void* one_args(lbm_ctx* c) {
+    if (c->n != 1) return nullptr;
+    return c->prec == LBM_FP32 ? static_cast<const void*>(&c->one_f) : static_cast<const void*>(&c->one_d);
+}
+
 int build_tiles(lbm_ctx* c) {
     const lbm::TileCfg t = lbm::step_config(c->prec, c->cfg);
     std::vector<std::vector<int4>> per(c->n);
@@ -310,6 +340,7 @@ int apply_schedule(lbm_ctx* c, int cfg, int sched) {
     CK(c, lbm::step_prepare(c->prec, cfg));
     int rc = encode_maps(c);
     if (rc) return rc;
+    refresh_one(c);
     rc = upload_insts(c);
     if (rc) return rc;
     return build_tiles(c);
@@ -380,7 +411,8 @@ int sync_all(lbm_ctx* c) {
 
 int launch_steps(lbm_ctx* c, int n) {
     for (int k = 0; k < n; ++k) {
-        CK(c, lbm::step_launch(c->prec, c->cfg, c->d_inst, c->d_tiles, c->ntiles, c->parity, kTimeoutNs, c->stream));
+        CK(c, lbm::step_launch(c->prec, c->cfg, c->d_inst, c->d_tiles, c->ntiles, c->parity, kTimeoutNs, one_args(c),
+                               c->stream));
         c->parity ^= 1;
         ++c->launches;
         ++c->steps;
@@ -394,7 +426,7 @@ int ensure_graph(lbm_ctx* c, int parity) {
     CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < kGraphSteps; ++k) {
         cudaError_t e = lbm::step_launch(c->prec, c->cfg, c->d_inst, c->d_tiles, c->ntiles, parity ^ (k & 1),
-                                         kTimeoutNs, c->stream);
+                                         kTimeoutNs, one_args(c), c->stream);
         if (e != cudaSuccess) {
             cudaStreamEndCapture(c->stream, &g);
             return cuda_fail(c, e, "step launch during graph capture");
@@ -624,6 +656,7 @@ int lbm_batch_set_params(lbm_ctx* c, int i, const lbm_eos* eos, double A, double
     hp.set = 1;
     fill_phys(c->h[i].pf, hp);
     fill_phys(c->h[i].pd, hp);
+    refresh_one(c);
     drop_graphs(c);
     return upload_insts(c);
 }
@@ -889,6 +922,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
     }
     std::fclose(fp);
     c->steps = hd.steps;
+    refresh_one(c);
     drop_graphs(c);
     CK(c, cudaMemset(c->d_status, 0, c->n * sizeof(int)));
     return upload_insts(c);

@@ -67,6 +67,18 @@ struct alignas(128) Inst {
     int pad_[3];
 };
 
+// Everything a single-lattice step needs, passed by value as a
+// __grid_constant__ kernel argument: the tensor maps and constants then live
+// in the parameter bank, and tile coordinates come from blockIdx.
+template <typename T> struct StepArgs {   // CUtensorMap members give it their alignment
+    CUtensorMap tmap[2];
+    Phys<T> P;
+    void* pop[2];
+    int* status;
+    long long plane;
+    int nx, ny, pitch, tiles_x;
+};
+
 template <typename T> __device__ __forceinline__ const Phys<T>& phys(const Inst* I);
 template <> __device__ __forceinline__ const Phys<float>& phys<float>(const Inst* I) { return I->pf; }
 template <> __device__ __forceinline__ const Phys<double>& phys<double>(const Inst* I) { return I->pd; }
@@ -170,8 +182,10 @@ int step_config_count(int prec);
 TileCfg step_config(int prec, int k);
 size_t step_smem_bytes(int prec, int k);
 cudaError_t step_prepare(int prec, int k);   // sets the dynamic smem attribute
+// one: a StepArgs<float> / StepArgs<double> for a context of one lattice
+// (tile coordinates from blockIdx), or nullptr to use the tile table.
 cudaError_t step_launch(int prec, int k, const Inst* d_insts, const int4* d_tiles, int ntiles,
-                        int parity, unsigned long long timeout_ns, cudaStream_t st);
+                        int parity, unsigned long long timeout_ns, const void* one, cudaStream_t st);
 
 // Auxiliary kernels (lbm_aux.cu); `host` is the host copy of the descriptor.
 cudaError_t aux_init(const Inst& host, const Inst* d_inst, const double* rho, const double* ux,

@@ -57,6 +57,11 @@ template <typename T> __device__ __forceinline__ T rho_dev(const T (&f)[9]) {
     return f[0] + Sa + Sd;
 }
 
+// Rounding is fixed by the source, not by the compiler: this file is built
+// with -fmad=false and every fused multiply-add is an explicit fma().  The
+// results are then the same bits for every tile shape, pipeline variant and
+// launch path the autotuner may pick.
+//
 // Product rounded on its own: never fused into an FMA with a neighbouring
 // add.  Used where a mirror or the x<->y transpose swaps two product terms
 // (p1^2 + p3^2, rho u_x^2 + rho u_y^2, ...): fma(a, a, b*b) is not
@@ -115,7 +120,7 @@ __device__ __forceinline__ void collide(const Regs<T>& P, const T (&f)[9], T Fx,
     const T Dxd = (f[5] - f[7]) + (f[8] - f[6]);
     const T Dyd = (f[5] - f[7]) + (f[6] - f[8]);
     const T jx = d13 + Dxd, jy = d24 + Dyd;
-    const T rux = jx + T(0.5) * Fx, ruy = jy + T(0.5) * Fy;   // rho v = j + F/2
+    const T rux = fma(T(0.5), Fx, jx), ruy = fma(T(0.5), Fy, jy);   // rho v = j + F/2
     const T ux = rux * inv, uy = ruy * inv;
     const T ru2 = mul_rn(rux, ux) + mul_rn(ruy, uy);   // rho |v|^2
     const T vF = mul_rn(ux, Fx) + mul_rn(uy, Fy);
@@ -128,17 +133,19 @@ __device__ __forceinline__ void collide(const Regs<T>& P, const T (&f)[9], T Fx,
     const T m7 = (f[1] + f[3]) - (f[2] + f[4]);
     const T m8 = (f[5] + f[7]) - (f[6] + f[8]);
 
-    const T e1 = T(3) * ru2 - T(2) * rt;               // m_eq deviations (Eq. 4)
-    const T e2 = rt - T(3) * ru2;
-    const T ms1 = m1 - P.s1 * (m1 - e1) + P.hs1 * (T(6) * vF) + P.c1 * trQ;
-    const T ms2 = m2 - P.s2 * (m2 - e2) - P.hs2 * (T(6) * vF) + P.c2 * trQ;
+    const T e1 = fma(T(3), ru2, T(-2) * rt);          // m_eq deviations (Eq. 4)
+    const T e2 = fma(T(-3), ru2, rt);
+    const T vF6 = T(6) * vF;
+    const T ms1 = fma(P.c1, trQ, fma(P.hs1, vF6, fma(-P.s1, m1 - e1, m1)));
+    const T ms2 = fma(P.c2, trQ, fma(-P.hs2, vF6, fma(-P.s2, m2 - e2, m2)));
     const T ms3 = jx + Fx;                             // = m3 - s_j (m3 - rho v_x) + (1 - s_j/2) F_x
-    const T ms4 = m4 - P.s4 * (m4 + rux) - P.hs4 * Fx;
+    const T ms4 = fma(-P.hs4, Fx, fma(-P.s4, m4 + rux, m4));
     const T ms5 = jy + Fy;
-    const T ms6 = m6 - P.s6 * (m6 + ruy) - P.hs6 * Fy;
-    const T ms7 = m7 - P.s7 * (m7 - (mul_rn(rux, ux) - mul_rn(ruy, uy))) +
-                  P.hs7 * (T(2) * (mul_rn(ux, Fx) - mul_rn(uy, Fy))) - P.s7 * (Qxx - Qyy);
-    const T ms8 = m8 - P.s8 * (m8 - rux * uy) + P.hs8 * (mul_rn(ux, Fy) + mul_rn(uy, Fx)) - P.s8 * Qxy;
+    const T ms6 = fma(-P.hs6, Fy, fma(-P.s6, m6 + ruy, m6));
+    const T ms7 = fma(-P.s7, Qxx - Qyy,
+                      fma(P.hs7, T(2) * (mul_rn(ux, Fx) - mul_rn(uy, Fy)),
+                          fma(-P.s7, m7 - (mul_rn(rux, ux) - mul_rn(ruy, uy)), m7)));
+    const T ms8 = fma(-P.s8, Qxy, fma(P.hs8, mul_rn(ux, Fy) + mul_rn(uy, Fx), fma(-P.s8, m8 - rux * uy, m8)));
 
     // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
     // The rows of a1..a8 sum to zero over the nine outputs, so the mass of the
@@ -183,24 +190,27 @@ template <typename T> __device__ __forceinline__ T radicand_step(const EosRegs<T
     T p;
     if (P.eos == LBM_EOS_CS) {
         const T n = P.b4 * rho, q = T(1) - n;
-        const T num = T(1) + n * (T(1) + n * (T(1) - n));
-        p = P.K * (Fast<T>::div(rho * P.RT * num, q * q * q) - P.a * rho * rho);
+        const T num = fma(n, fma(n, T(1) - n, T(1)), T(1));
+        p = P.K * fma(-P.a * rho, rho, Fast<T>::div(rho * P.RT * num, q * q * q));
     } else if (P.eos == LBM_EOS_VDW) {
-        p = P.K * (Fast<T>::div(rho * P.RT, T(1) - P.b * rho) - P.a * rho * rho);
+        p = P.K * fma(-P.a * rho, rho, Fast<T>::div(rho * P.RT, fma(-P.b, rho, T(1))));
     } else {
         const T br = P.b * rho;
-        p = P.K * (Fast<T>::div(rho * P.RT, T(1) - br) -
-                   Fast<T>::div(P.aalpha * rho * rho, T(1) + T(2) * br - br * br));
+        p = P.K * (Fast<T>::div(rho * P.RT, T(1) - br) - Fast<T>::div(P.aalpha * rho * rho, fma(br, T(2) - br, T(1))));
     }
-    return P.two_over_G * (p - rho * T(1.0 / 3.0));
+    return P.two_over_G * fma(rho, T(-1.0 / 3.0), p);
 }
 
-// Persistent CTA over a strided list of tiles with a two-stage TMA pipeline:
-// while tile k is collided, the box of tile k+1 streams into the other
-// shared-memory buffer.
-template <typename T, int BX, int BY, int NT, int NBUF>
+// One kernel, two ways to find the work: ONE = a single lattice whose
+// constants and tensor maps arrive in the __grid_constant__ argument, tile
+// coordinates from the tile index; otherwise a tile table over instances
+// whose descriptors live in global memory.  NBUF = 2 makes the CTAs
+// persistent with a two-stage TMA pipeline: while tile k is collided, the
+// box of tile k+1 streams into the other shared-memory buffer.
+template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
 __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, const int4* __restrict__ tiles,
-                                             int ntiles, int parity, unsigned long long timeout_ns) {
+                                             int ntiles, int parity, unsigned long long timeout_ns,
+                                             const __grid_constant__ StepArgs<T> one) {
     using Gm = Geom<T, BX, BY, NT, NBUF>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -216,16 +226,29 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
     }
     __syncthreads();
 
+    auto tile_of = [&](int tt, int& inst, int& x0, int& y0) {
+        if (ONE) {
+            inst = 0;
+            x0 = (tt % one.tiles_x) * BX;
+            y0 = (tt / one.tiles_x) * BY;
+        } else {
+            const int4 tl = tiles[tt];
+            inst = tl.x;
+            x0 = tl.y;
+            y0 = tl.z;
+        }
+    };
     int last_inst = -1;   // thread 0 only: instance whose tensor map was last acquired
     auto issue = [&](int tt, int bb) {
-        const int4 tl = tiles[tt];
-        const CUtensorMap* map = &insts[tl.x].tmap[parity];
-        if (tl.x != last_inst) {
+        int inst, x0, y0;
+        tile_of(tt, inst, x0, y0);
+        const CUtensorMap* map = ONE ? &one.tmap[parity] : &insts[inst].tmap[parity];
+        if (!ONE && inst != last_inst) {
             acquire_tmap(map);
-            last_inst = tl.x;
+            last_inst = inst;
         }
         mbar_arrive_expect_tx(&bar[bb], static_cast<uint32_t>(Gm::box_bytes));
-        tma_load_3d(smem + bb * Gm::buf_stride, map, tl.y + Gm::GX - Gm::HX, tl.z, 0, &bar[bb]);
+        tma_load_3d(smem + bb * Gm::buf_stride, map, x0 + Gm::GX - Gm::HX, y0, 0, &bar[bb]);
     };
     if (tid == 0) issue(t, 0);
 
@@ -236,11 +259,12 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
         const uint32_t ph = NBUF == 2 ? ((k >> 1) & 1) : (k & 1);
         const T* sf = reinterpret_cast<const T*>(smem + b * Gm::buf_stride);
         T* sp = reinterpret_cast<T*>(smem + Gm::psi_off + b * Gm::psi_stride);
-        const int4 tile = tiles[t];
-        const Inst* I = insts + tile.x;
-        const int x0 = tile.y, y0 = tile.z;
-        const Phys<T>& P = phys<T>(I);
-        const int nx = I->nx, ny = I->ny;
+        int inst, x0, y0;
+        tile_of(t, inst, x0, y0);
+        const Inst* I = ONE ? nullptr : insts + inst;
+        const Phys<T>& P = ONE ? one.P : phys<T>(I);
+        const int nx = ONE ? one.nx : I->nx, ny = ONE ? one.ny : I->ny;
+        int* status = ONE ? one.status : I->status;
         const int interact = P.interact;
         const EosRegs<T> E(P);
         const Regs<T> R(P);
@@ -266,14 +290,13 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
                     y0 - 1 + j < ny)
                     bad = true;
             };
-            for (int j = ty; j < Gm::HP; j += Gm::TY) {
-                ring(tx, j);
-                if (tx < 2) ring(BX + tx, j);
-            }
+            for (int j = ty; j < Gm::HP; j += Gm::TY) ring(tx, j);
+            // the ring's two right-hand columns, spread over the first threads
+            for (int e = tid; e < 2 * Gm::HP; e += NT) ring(BX + (e & 1), e >> 1);
         }
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
-                atomicOr(I->status, ST_TIMEOUT);
+                atomicOr(status, ST_TIMEOUT);
                 mbar_wait_bounded(&bar[b], ph, timeout_ns);   // let a late copy land before exit
             }
             return;
@@ -282,118 +305,151 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
         if (NBUF == 2 && tid == 0 && t + static_cast<int>(gridDim.x) < ntiles) issue(t + gridDim.x, b ^ 1);
 
         // ---- collide and stream every owned node -------------------------
-        T* __restrict__ dst = static_cast<T*>(I->pop[parity ^ 1]);
-        const long long plane = I->plane;
-        const int pitch = I->pitch;
+        // each thread owns ROWS consecutive rows of one column; the 3x3 psi
+        // neighbourhood slides down with it (three new loads per node)
+        T* __restrict__ dst = static_cast<T*>(ONE ? one.pop[parity ^ 1] : I->pop[parity ^ 1]);
+        const long long plane = ONE ? one.plane : I->plane;
+        const int pitch = ONE ? one.pitch : I->pitch;
         const T G = P.G, A = P.A;
         const T hA = T(0.5) * A, omA = T(1) - A;
         const T kG2 = P.kappa * G * T(0.5);
         const bool border = x0 < 2 || x0 + BX > nx - 2 || y0 < 2 || y0 + BY > ny - 2;
+        const int ly0 = ty * Gm::ROWS;
+        const T* s0 = sp + (ly0 + 1) * Gm::WP + (tx + 1);   // psi of node (tx, ly0)
+        T wm0 = T(0), wm1 = T(0), wm2 = T(0), w00 = T(0), w01 = T(0), w02 = T(0);
+        if (interact) {
+            wm0 = s0[-Gm::WP - 1];
+            wm1 = s0[-Gm::WP];
+            wm2 = s0[-Gm::WP + 1];
+            w00 = s0[-1];
+            w01 = s0[0];
+            w02 = s0[1];
+        }
 
-#pragma unroll 1
+#pragma unroll
         for (int r = 0; r < Gm::ROWS; ++r) {
-            const int ly = ty + r * Gm::TY;
+            const int ly = ly0 + r;
             const int x = x0 + tx, y = y0 + ly;
-            if (x >= nx || y >= ny) continue;
-            const T* q = sf + (ly + GY) * Gm::WB + (tx + Gm::HX);
-            T f[9];
-#pragma unroll
-            for (int a = 0; a < 9; ++a) f[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
-
-            T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
+            T wp0 = T(0), wp1 = T(0), wp2 = T(0);
             if (interact) {
-                const T* s = sp + (ly + 1) * Gm::WP + (tx + 1);
-                const T p0 = s[0];
-                const T p1 = s[1], p2 = s[Gm::WP], p3 = s[-1], p4 = s[-Gm::WP];
-                const T p5 = s[Gm::WP + 1], p6 = s[Gm::WP - 1], p7 = s[-Gm::WP - 1], p8 = s[-Gm::WP + 1];
-                const T q1 = mul_rn(p1, p1), q2 = mul_rn(p2, p2), q3 = mul_rn(p3, p3), q4 = mul_rn(p4, p4);
-                const T q5 = mul_rn(p5, p5), q6 = mul_rn(p6, p6), q7 = mul_rn(p7, p7), q8 = mul_rn(p8, p8);
-                // Eq. 9: F = -G [ (A/2) sum w psi_n^2 e + (1-A) psi sum w psi_n e ]
-                const T gx1 = w1 * (p1 - p3) + w2 * ((p5 - p7) + (p8 - p6));
-                const T gy1 = w1 * (p2 - p4) + w2 * ((p5 - p7) + (p6 - p8));
-                const T gx2 = w1 * (q1 - q3) + w2 * ((q5 - q7) + (q8 - q6));
-                const T gy2 = w1 * (q2 - q4) + w2 * ((q5 - q7) + (q6 - q8));
-                Fx = -G * (hA * gx2 + omA * p0 * gx1);
-                Fy = -G * (hA * gy2 + omA * p0 * gy1);
-                // Eq. 23 (x G/2): sums of w (psi_n - psi) e e and w (psi_n^2 - psi^2) e e;
-                // sum w e_x^2 = sum w e_y^2 = 1 and sum w e_x e_y = 0 over the ring
-                const T d1 = w2 * ((p5 + p7) + (p6 + p8));
-                const T d2 = w2 * ((q5 + q7) + (q6 + q8));
-                const T q0 = mul_rn(p0, p0);
-                const T sxx1 = w1 * (p1 + p3) + d1 - p0, syy1 = w1 * (p2 + p4) + d1 - p0;
-                const T sxy1 = w2 * ((p5 + p7) - (p6 + p8));
-                const T sxx2 = w1 * (q1 + q3) + d2 - q0, syy2 = w1 * (q2 + q4) + d2 - q0;
-                const T sxy2 = w2 * ((q5 + q7) - (q6 + q8));
-                const T c = omA * p0;
-                Qxx = kG2 * (c * sxx1 + hA * sxx2);
-                Qyy = kG2 * (c * syy1 + hA * syy2);
-                Qxy = kG2 * (c * sxy1 + hA * sxy2);
+                const T* sr = s0 + (r + 1) * Gm::WP;
+                wp0 = sr[-1];
+                wp1 = sr[0];
+                wp2 = sr[1];
             }
-
-            T out[9];
-            collide(R, f, Fx, Fy, Qxx, Qyy, Qxy, out);
-            if (!(out[0] == out[0])) bad = true;
-
-            T* o = dst + static_cast<long long>(y + GY) * pitch + (x + Gm::GX);
+            if (x < nx && y < ny) {
+                const T* q = sf + (ly + GY) * Gm::WB + (tx + Gm::HX);
+                T f[9];
 #pragma unroll
-            for (int a = 0; a < 9; ++a) o[a * plane] = out[a];
+                for (int a = 0; a < 9; ++a) f[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
 
-            // periodic images in the ghost cells read by the neighbouring tiles
-            if (border) {
-                const bool xl = x < 2, xr = x >= nx - 2, yl = y < 2, yr = y >= ny - 2;
-                if (xl || xr || yl || yr) {
-                    const int oxs[3] = {0, xl ? nx : 0, xr ? -nx : 0};
-                    const int oys[3] = {0, yl ? ny : 0, yr ? -ny : 0};
-                    const bool hx[3] = {true, xl, xr};
-                    const bool hy[3] = {true, yl, yr};
-                    for (int iy = 0; iy < 3; ++iy)
-                        for (int ix = 0; ix < 3; ++ix) {
-                            if (!(hx[ix] && hy[iy]) || (ix == 0 && iy == 0)) continue;
-                            T* g = o + static_cast<long long>(oys[iy]) * pitch + oxs[ix];
+                T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
+                if (interact) {
+                    const T p0 = w01;
+                    const T p1 = w02, p2 = wp1, p3 = w00, p4 = wm1;
+                    const T p5 = wp2, p6 = wp0, p7 = wm0, p8 = wm2;
+                    const T q1 = mul_rn(p1, p1), q2 = mul_rn(p2, p2), q3 = mul_rn(p3, p3), q4 = mul_rn(p4, p4);
+                    const T q5 = mul_rn(p5, p5), q6 = mul_rn(p6, p6), q7 = mul_rn(p7, p7), q8 = mul_rn(p8, p8);
+                    // Eq. 9: F = -G [ (A/2) sum w psi_n^2 e + (1-A) psi sum w psi_n e ]
+                    const T gx1 = fma(w1, p1 - p3, w2 * ((p5 - p7) + (p8 - p6)));
+                    const T gy1 = fma(w1, p2 - p4, w2 * ((p5 - p7) + (p6 - p8)));
+                    const T gx2 = fma(w1, q1 - q3, w2 * ((q5 - q7) + (q8 - q6)));
+                    const T gy2 = fma(w1, q2 - q4, w2 * ((q5 - q7) + (q6 - q8)));
+                    const T c = omA * p0;
+                    Fx = -G * fma(c, gx1, hA * gx2);
+                    Fy = -G * fma(c, gy1, hA * gy2);
+                    // Eq. 23 (x G/2): sums of w (psi_n - psi) e e and w (psi_n^2 - psi^2) e e;
+                    // sum w e_x^2 = sum w e_y^2 = 1 and sum w e_x e_y = 0 over the ring
+                    const T d1 = w2 * ((p5 + p7) + (p6 + p8));
+                    const T d2 = w2 * ((q5 + q7) + (q6 + q8));
+                    const T q0 = mul_rn(p0, p0);
+                    const T sxx1 = fma(w1, p1 + p3, d1) - p0, syy1 = fma(w1, p2 + p4, d1) - p0;
+                    const T sxy1 = w2 * ((p5 + p7) - (p6 + p8));
+                    const T sxx2 = fma(w1, q1 + q3, d2) - q0, syy2 = fma(w1, q2 + q4, d2) - q0;
+                    const T sxy2 = w2 * ((q5 + q7) - (q6 + q8));
+                    Qxx = kG2 * fma(c, sxx1, hA * sxx2);
+                    Qyy = kG2 * fma(c, syy1, hA * syy2);
+                    Qxy = kG2 * fma(c, sxy1, hA * sxy2);
+                }
+
+                T out[9];
+                collide(R, f, Fx, Fy, Qxx, Qyy, Qxy, out);
+                if (!(out[0] == out[0])) bad = true;
+
+                T* o = dst + static_cast<long long>(y + GY) * pitch + (x + Gm::GX);
 #pragma unroll
-                            for (int a = 0; a < 9; ++a) g[a * plane] = out[a];
-                        }
+                for (int a = 0; a < 9; ++a) o[a * plane] = out[a];
+
+                // periodic images in the ghost cells read by the neighbouring tiles
+                if (border) {
+                    const bool xl = x < 2, xr = x >= nx - 2, yl = y < 2, yr = y >= ny - 2;
+                    if (xl || xr || yl || yr) {
+                        const int oxs[3] = {0, xl ? nx : 0, xr ? -nx : 0};
+                        const int oys[3] = {0, yl ? ny : 0, yr ? -ny : 0};
+                        const bool hx[3] = {true, xl, xr};
+                        const bool hy[3] = {true, yl, yr};
+                        for (int iy = 0; iy < 3; ++iy)
+                            for (int ix = 0; ix < 3; ++ix) {
+                                if (!(hx[ix] && hy[iy]) || (ix == 0 && iy == 0)) continue;
+                                T* g = o + static_cast<long long>(oys[iy]) * pitch + oxs[ix];
+#pragma unroll
+                                for (int a = 0; a < 9; ++a) g[a * plane] = out[a];
+                            }
+                    }
                 }
             }
+            wm0 = w00; wm1 = w01; wm2 = w02;
+            w00 = wp0; w01 = wp1; w02 = wp2;
         }
-        if (bad) atomicOr(I->status, ST_UNSTABLE);
+        if (bad) atomicOr(status, ST_UNSTABLE);
     }
 }
 
 // ---- tile configurations ------------------------------------------------
 template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
     using Gm = Geom<T, BX, BY, NT, NBUF>;
-    static int grid_cap;   // resident CTAs on the device (persistent grid)
+    static int grid_cap[2];   // resident CTAs on the device (persistent grid), per kernel variant
     static TileCfg tc() { return TileCfg{BX, BY, NT, NBUF}; }
     static size_t smem() { return Gm::smem; }
-    static cudaError_t prepare() {
-        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, NT, NBUF>,
+    template <bool ONE> static cudaError_t prep_one() {
+        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, NT, NBUF, ONE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(Gm::smem));
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, occ = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<T, BX, BY, NT, NBUF>, NT, Gm::smem)) !=
-            cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<T, BX, BY, NT, NBUF, ONE>, NT,
+                                                                Gm::smem)) != cudaSuccess)
             return e;
-        grid_cap = (occ > 0 ? occ : 1) * sms;
+        grid_cap[ONE ? 1 : 0] = (occ > 0 ? occ : 1) * sms;
         return cudaSuccess;
     }
-    static cudaError_t launch(const Inst* d, const int4* t, int n, int parity, unsigned long long to,
+    static cudaError_t prepare() {
+        cudaError_t e = prep_one<false>();
+        return e != cudaSuccess ? e : prep_one<true>();
+    }
+    static cudaError_t launch(const Inst* d, const int4* t, int n, int parity, unsigned long long to, const void* one,
                               cudaStream_t st) {
         // one CTA per tile, or a persistent grid of resident CTAs striding over the tiles
-        const int grid = NBUF == 1 ? n : (n < grid_cap ? n : grid_cap);
-        k_step<T, BX, BY, NT, NBUF><<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to);
+        const int cap = grid_cap[one ? 1 : 0];
+        const int grid = NBUF == 1 ? n : (n < cap ? n : cap);
+        if (one) {
+            k_step<T, BX, BY, NT, NBUF, true><<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to,
+                                                                          *static_cast<const StepArgs<T>*>(one));
+        } else {
+            static const StepArgs<T> none{};
+            k_step<T, BX, BY, NT, NBUF, false><<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to, none);
+        }
         return cudaGetLastError();
     }
 };
-template <typename T, int BX, int BY, int NT, int NBUF> int Cfg<T, BX, BY, NT, NBUF>::grid_cap = 1;
+template <typename T, int BX, int BY, int NT, int NBUF> int Cfg<T, BX, BY, NT, NBUF>::grid_cap[2] = {1, 1};
 
 struct Entry {
     TileCfg (*tc)();
     size_t (*smem)();
     cudaError_t (*prepare)();
-    cudaError_t (*launch)(const Inst*, const int4*, int, int, unsigned long long, cudaStream_t);
+    cudaError_t (*launch)(const Inst*, const int4*, int, int, unsigned long long, const void*, cudaStream_t);
     int nbuf;
 };
 
@@ -446,10 +502,10 @@ cudaError_t step_prepare(int prec, int k) {
 }
 
 cudaError_t step_launch(int prec, int k, const Inst* d_insts, const int4* d_tiles, int ntiles, int parity,
-                        unsigned long long timeout_ns, cudaStream_t st) {
+                        unsigned long long timeout_ns, const void* one, cudaStream_t st) {
     int n;
     const Entry* e = table(prec, &n);
-    return e[k].launch(d_insts, d_tiles, ntiles, parity, timeout_ns, st);
+    return e[k].launch(d_insts, d_tiles, ntiles, parity, timeout_ns, one, st);
 }
 
 }  // namespace lbm
