@@ -127,6 +127,17 @@ int lbm_set_params(lbm_ctx* ctx, const lbm_eos* eos, double A, double kappa, dou
 int lbm_batch_set_params(lbm_ctx* ctx, int i, const lbm_eos* eos, double A, double kappa,
                          double G, const double s[9], double rho_ref, unsigned flags);
 
+/* Density-dependent shear viscosity (Section 4.2: gas and liquid of
+ * different viscosity): with enable != 0, nu(rho) is linear between
+ * (rho_gas, nu_gas) and (rho_liquid, nu_liquid) and clamped to that range, and
+ * the shear rates become s_7 = s_8 = 1 / (3 nu(rho) + 1/2) at every node,
+ * replacing s[7], s[8].  enable = 0 restores the fixed rates.  Call after
+ * lbm_set_params; a later lbm_set_params keeps the law. */
+int lbm_set_viscosity(lbm_ctx* ctx, int enable, double nu_gas, double nu_liquid, double rho_gas,
+                      double rho_liquid);
+int lbm_batch_set_viscosity(lbm_ctx* ctx, int i, int enable, double nu_gas, double nu_liquid,
+                            double rho_gas, double rho_liquid);
+
 /* Initial state f_a = M^-1 m_eq(rho, u) (Eq. 4) from host fields of nx*ny
  * doubles; ux, uy may be NULL (zero velocity).  Resets the step counter and
  * the instance's status. */

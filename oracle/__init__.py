@@ -33,6 +33,9 @@ class _Params(ctypes.Structure):
         ("li_eps", ctypes.c_int), ("no_q", ctypes.c_int),
         ("fext_x", ctypes.c_double), ("fext_y", ctypes.c_double),
         ("walls_y", ctypes.c_int),
+        ("var_visc", ctypes.c_int),
+        ("nu_g", ctypes.c_double), ("nu_l", ctypes.c_double),
+        ("visc_rho_g", ctypes.c_double), ("visc_rho_l", ctypes.c_double),
     ]
 
 
@@ -57,16 +60,23 @@ class Params:
     fext_x: float = 0.0
     fext_y: float = 0.0
     walls_y: bool = False
+    var_visc: bool = False
+    nu_g: float = 0.0
+    nu_l: float = 0.0
+    visc_rho_g: float = 0.0
+    visc_rho_l: float = 1.0
 
     def c(self) -> _Params:
         p = _Params()
         p.eos = int(self.eos)
-        for k in ("a", "b", "R", "K", "T", "omega", "Tc", "A", "kappa", "G", "fext_x", "fext_y"):
+        for k in ("a", "b", "R", "K", "T", "omega", "Tc", "A", "kappa", "G", "fext_x", "fext_y", "nu_g", "nu_l",
+                  "visc_rho_g", "visc_rho_l"):
             setattr(p, k, float(getattr(self, k)))
         p.s = (ctypes.c_double * 9)(*[float(v) for v in self.s])
         p.li_eps = int(bool(self.li_eps))
         p.no_q = int(bool(self.no_q))
         p.walls_y = int(bool(self.walls_y))
+        p.var_visc = int(bool(self.var_visc))
         return p
 
 

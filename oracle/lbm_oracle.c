@@ -57,6 +57,11 @@ typedef struct {
     int no_q;         /* 1: Q and C are not evaluated at all (unmodified model) */
     double fext_x, fext_y;  /* test-only constant body-force density */
     int walls_y;      /* test-only: half-way bounce-back walls at y=-1/2 and y=ny-1/2 */
+    /* Density-dependent shear viscosity (Section 4.2): when var_visc is set,
+     * nu(rho) is linear between (rho_g, nu_g) and (rho_l, nu_l), clamped to
+     * that range, and s_7 = s_8 = 1/(3 nu + 1/2). */
+    int var_visc;
+    double nu_g, nu_l, visc_rho_g, visc_rho_l;
 } orc_params;
 
 /* D2Q9 velocities e_0..e_8: rest, four axis neighbours, four diagonals. */
@@ -217,6 +222,16 @@ void orc_force_q(const orc_params *p, int nx, int ny, const double *psi,
 
 /* Eq. 25 at one node: m* = m - Lambda (m - m_eq) + (I - Lambda/2) S + C,
  * then f* = M^-1 m*.  Velocity by R2. */
+/* Relaxation rate of the shear moments (p_xx, p_xy) at density rho. */
+static double shear_rate(const orc_params *p, double rho) {
+    if (!p->var_visc) return p->s[7];
+    double w = (rho - p->visc_rho_g) / (p->visc_rho_l - p->visc_rho_g);
+    if (w < 0.0) w = 0.0;
+    if (w > 1.0) w = 1.0;
+    double nu = p->nu_g + w * (p->nu_l - p->nu_g);
+    return 1.0 / (3.0 * nu + 0.5);
+}
+
 static void collide(const orc_params *p, double Minv[Q9][Q9], const double *f, double Fx,
                     double Fy, double Qxx, double Qyy, double Qxy, double *fout) {
     double rho = 0.0, jx = 0.0, jy = 0.0;
@@ -234,13 +249,16 @@ static void collide(const orc_params *p, double Minv[Q9][Q9], const double *f, d
     }
     orc_meq(rho, vx, vy, meq);
     orc_source_s(vx, vy, Fx, Fy, S);
+    /* the rates of this node: the shear pair may depend on density */
+    orc_params pl = *p;
+    pl.s[7] = pl.s[8] = shear_rate(p, rho);
     if (p->no_q) {
         for (int k = 0; k < Q9; ++k) C[k] = 0.0;
     } else {
-        orc_source_c(p, Qxx, Qyy, Qxy, C);
+        orc_source_c(&pl, Qxx, Qyy, Qxy, C);
     }
     for (int k = 0; k < Q9; ++k) {
-        ms[k] = m[k] - p->s[k] * (m[k] - meq[k]) + (1.0 - p->s[k] / 2.0) * S[k];
+        ms[k] = m[k] - pl.s[k] * (m[k] - meq[k]) + (1.0 - pl.s[k] / 2.0) * S[k];
         if (!p->no_q) ms[k] = ms[k] + C[k];
     }
     for (int a = 0; a < Q9; ++a) {

@@ -24,6 +24,8 @@ struct HostParams {
     double A, kappa, G, s[9], rho_ref;
     unsigned flags;
     int set;
+    int var_visc;
+    double nu_g, nu_l, visc_rho_g, visc_rho_l;
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -374,6 +376,11 @@ template <typename T> void fill_phys(lbm::Phys<T>& P, const HostParams& hp) {
     P.c1 = T(1.5 * hp.s[1]);
     P.c2 = (hp.flags & LBM_FLAG_LI_EPS) ? T(-1.5 * hp.s[2]) : T(0);
     P.rho_ref = T(hp.rho_ref);
+    P.var_visc = hp.var_visc;
+    P.nu_g = T(hp.nu_g);
+    P.dnu = T(hp.nu_l - hp.nu_g);
+    P.visc_rho_g = T(hp.visc_rho_g);
+    P.visc_inv_drho = hp.var_visc ? T(1.0 / (hp.visc_rho_l - hp.visc_rho_g)) : T(0);
 }
 
 int check_idx(lbm_ctx* c, int i) {
@@ -646,6 +653,7 @@ int lbm_batch_set_params(lbm_ctx* c, int i, const lbm_eos* eos, double A, double
     if (!valid_params(eos, A, kappa, G, s, rho_ref)) return fail(c, LBM_EINVAL, "invalid model parameters%s");
     CK(c, cudaSetDevice(c->device));
     HostParams& hp = c->hp[i];
+    const HostParams keep = hp;
     hp.eos = *eos;
     hp.A = A;
     hp.kappa = kappa;
@@ -654,6 +662,11 @@ int lbm_batch_set_params(lbm_ctx* c, int i, const lbm_eos* eos, double A, double
     hp.rho_ref = rho_ref;
     hp.flags = flags;
     hp.set = 1;
+    hp.var_visc = keep.set ? keep.var_visc : 0;   // the viscosity law survives a parameter change
+    hp.nu_g = keep.nu_g;
+    hp.nu_l = keep.nu_l;
+    hp.visc_rho_g = keep.visc_rho_g;
+    hp.visc_rho_l = keep.visc_rho_l;
     fill_phys(c->h[i].pf, hp);
     fill_phys(c->h[i].pd, hp);
     refresh_one(c);
@@ -664,6 +677,32 @@ int lbm_batch_set_params(lbm_ctx* c, int i, const lbm_eos* eos, double A, double
 int lbm_set_params(lbm_ctx* c, const lbm_eos* eos, double A, double kappa, double G, const double s[9], double rho_ref,
                    unsigned flags) {
     return lbm_batch_set_params(c, 0, eos, A, kappa, G, s, rho_ref, flags);
+}
+
+int lbm_batch_set_viscosity(lbm_ctx* c, int i, int enable, double nu_gas, double nu_liquid, double rho_gas,
+                            double rho_liquid) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!c->hp[i].set) return fail(c, LBM_EINVAL, "set the parameters before the viscosity law%s");
+    if (enable && (!(nu_gas > 0) || !(nu_liquid > 0) || !(rho_liquid > rho_gas) || !std::isfinite(rho_liquid) ||
+                   !std::isfinite(nu_gas + nu_liquid + rho_gas)))
+        return fail(c, LBM_EINVAL, "viscosities must be positive and rho_liquid > rho_gas%s");
+    CK(c, cudaSetDevice(c->device));
+    HostParams& hp = c->hp[i];
+    hp.var_visc = enable ? 1 : 0;
+    hp.nu_g = nu_gas;
+    hp.nu_l = nu_liquid;
+    hp.visc_rho_g = rho_gas;
+    hp.visc_rho_l = rho_liquid;
+    fill_phys(c->h[i].pf, hp);
+    fill_phys(c->h[i].pd, hp);
+    refresh_one(c);
+    drop_graphs(c);
+    return upload_insts(c);
+}
+
+int lbm_set_viscosity(lbm_ctx* c, int enable, double nu_gas, double nu_liquid, double rho_gas, double rho_liquid) {
+    return lbm_batch_set_viscosity(c, 0, enable, nu_gas, nu_liquid, rho_gas, rho_liquid);
 }
 
 int lbm_batch_init_density(lbm_ctx* c, int i, const double* rho, const double* ux, const double* uy) {
@@ -865,7 +904,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
     if (!fp) return fail(c, LBM_EIO, "cannot open %s for writing", path);
     CkptHeader hd{};
     std::memcpy(hd.magic, "LBMCKPT1", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.n = c->n;
     hd.prec = c->prec;
     hd.steps = c->steps;
@@ -891,7 +930,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(c, LBM_EIO, "cannot open %s", path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, "LBMCKPT1", 8) != 0 || hd.version != 1 ||
+    if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, "LBMCKPT1", 8) != 0 || hd.version != 2 ||
         hd.n != c->n || hd.prec != c->prec) {
         std::fclose(fp);
         return fail(c, LBM_EIO, "%s is not a checkpoint of this context's shape and precision", path);

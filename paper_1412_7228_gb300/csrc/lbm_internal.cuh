@@ -51,6 +51,10 @@ template <typename T> struct Phys {
     T c1, c2;           // C[1] = c1 tr Q, C[2] = c2 tr Q (Eq. 26)
     T rho_ref;          // deviation reference
     int interact;       // 0 when G == 0: no psi, F = Q = 0
+    // density-dependent shear viscosity: nu(rho) linear between (rho_g, nu_g)
+    // and (rho_l, nu_l), clamped; s_7 = s_8 = 1 / (3 nu + 1/2)
+    int var_visc;
+    T nu_g, dnu, visc_rho_g, visc_inv_drho;
 };
 
 // One lattice.  The two tensor maps come first: a CUtensorMap must sit on a

@@ -99,10 +99,13 @@ template <> struct Fast<double> {
 // issue slots, keeps references and spends its registers on occupancy.
 template <typename T, typename V> struct RegsOf {
     V s1, s2, s4, s6, s7, s8, hs1, hs2, hs4, hs6, hs7, hs8, c1, c2, rho_ref;
+    int var_visc;
+    V nu_g, dnu, visc_rho_g, visc_inv_drho;
     __device__ __forceinline__ explicit RegsOf(const Phys<T>& P)
         : s1(P.s[1]), s2(P.s[2]), s4(P.s[4]), s6(P.s[6]), s7(P.s[7]), s8(P.s[8]), hs1(P.hs[1]),
           hs2(P.hs[2]), hs4(P.hs[4]), hs6(P.hs[6]), hs7(P.hs[7]), hs8(P.hs[8]), c1(P.c1), c2(P.c2),
-          rho_ref(P.rho_ref) {}
+          rho_ref(P.rho_ref), var_visc(P.var_visc), nu_g(P.nu_g), dnu(P.dnu), visc_rho_g(P.visc_rho_g),
+          visc_inv_drho(P.visc_inv_drho) {}
 };
 template <typename T> struct RegsSel { using type = RegsOf<T, const T&>; };
 template <> struct RegsSel<float> { using type = RegsOf<float, float>; };
@@ -142,10 +145,18 @@ __device__ __forceinline__ void collide(const Regs<T>& P, const T (&f)[9], T Fx,
     const T ms4 = fma(-P.hs4, Fx, fma(-P.s4, m4 + rux, m4));
     const T ms5 = jy + Fy;
     const T ms6 = fma(-P.hs6, Fy, fma(-P.s6, m6 + ruy, m6));
-    const T ms7 = fma(-P.s7, Qxx - Qyy,
-                      fma(P.hs7, T(2) * (mul_rn(ux, Fx) - mul_rn(uy, Fy)),
-                          fma(-P.s7, m7 - (mul_rn(rux, ux) - mul_rn(ruy, uy)), m7)));
-    const T ms8 = fma(-P.s8, Qxy, fma(P.hs8, mul_rn(ux, Fy) + mul_rn(uy, Fx), fma(-P.s8, m8 - rux * uy, m8)));
+    // shear rates: fixed, or from the density-dependent viscosity (Section 4.2)
+    T s7 = P.s7, s8 = P.s8, hs7 = P.hs7, hs8 = P.hs8;
+    if (P.var_visc) {
+        const T w = fmin(fmax((rho - P.visc_rho_g) * P.visc_inv_drho, T(0)), T(1));
+        const T sn = Fast<T>::rcp(fma(T(3), fma(w, P.dnu, P.nu_g), T(0.5)));
+        s7 = s8 = sn;
+        hs7 = hs8 = fma(T(-0.5), sn, T(1));
+    }
+    const T ms7 = fma(-s7, Qxx - Qyy,
+                      fma(hs7, T(2) * (mul_rn(ux, Fx) - mul_rn(uy, Fy)),
+                          fma(-s7, m7 - (mul_rn(rux, ux) - mul_rn(ruy, uy)), m7)));
+    const T ms8 = fma(-s8, Qxy, fma(hs8, mul_rn(ux, Fy) + mul_rn(uy, Fx), fma(-s8, m8 - rux * uy, m8)));
 
     // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
     // The rows of a1..a8 sum to zero over the nine outputs, so the mass of the

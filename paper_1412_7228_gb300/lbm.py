@@ -31,7 +31,8 @@ _CODES = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA", LBM_EU
 EXPORTS = [
     "lbm_eos_pressure", "lbm_eos_critical", "lbm_eos_maxwell", "lbm_laplace_fit",
     "lbm_required_bytes", "lbm_batch_required_bytes", "lbm_create", "lbm_batch_create", "lbm_destroy",
-    "lbm_set_params", "lbm_batch_set_params", "lbm_init_density", "lbm_batch_init_density",
+    "lbm_set_params", "lbm_batch_set_params", "lbm_set_viscosity", "lbm_batch_set_viscosity",
+    "lbm_init_density", "lbm_batch_init_density",
     "lbm_step", "lbm_sync", "lbm_status", "lbm_clear_status",
     "lbm_read_fields", "lbm_batch_read_fields", "lbm_read_populations", "lbm_batch_read_populations",
     "lbm_measure_pressure_jump", "lbm_batch_measure", "lbm_stats", "lbm_batch_stats",
@@ -102,6 +103,8 @@ def lib():
                             ctypes.c_uint], ctypes.c_int),
         "lbm_batch_set_params": ([_vp, ctypes.c_int, E, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
                                   ctypes.c_double, ctypes.c_uint], ctypes.c_int),
+        "lbm_set_viscosity": ([_vp, ctypes.c_int] + [ctypes.c_double] * 4, ctypes.c_int),
+        "lbm_batch_set_viscosity": ([_vp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4, ctypes.c_int),
         "lbm_init_density": ([_vp, _dp, _dp, _dp], ctypes.c_int),
         "lbm_batch_init_density": ([_vp, ctypes.c_int, _dp, _dp, _dp], ctypes.c_int),
         "lbm_step": ([_vp, ctypes.c_int], ctypes.c_int),
@@ -298,6 +301,10 @@ class Batch:
         sv = (ctypes.c_double * 9)(*[float(v) for v in s])
         self._c(lib().lbm_batch_set_params(self.ctx, i, ctypes.byref(eos.c()), A, kappa, G, sv, rho_ref, flags))
 
+    def set_viscosity(self, i: int, nu_gas: float, nu_liquid: float, rho_gas: float, rho_liquid: float,
+                      enable: bool = True):
+        self._c(lib().lbm_batch_set_viscosity(self.ctx, i, int(enable), nu_gas, nu_liquid, rho_gas, rho_liquid))
+
     def init_density(self, i: int, rho, ux=None, uy=None):
         shape = (self.ny[i], self.nx[i])
         r, u, v = _f64(rho, shape), _f64(ux, shape), _f64(uy, shape)
@@ -381,6 +388,10 @@ class Lattice(Batch):
 
     def measure_pressure_jump(self, cx: float, cy: float, r_in: float, r_out: float) -> dict:
         return self.measure(0, cx, cy, r_in, r_out)
+
+    def set_viscosity(self, nu_gas: float, nu_liquid: float, rho_gas: float, rho_liquid: float,
+                      enable: bool = True):
+        super().set_viscosity(0, nu_gas, nu_liquid, rho_gas, rho_liquid, enable)
 
 
 # ---- learned surrogate --------------------------------------------------

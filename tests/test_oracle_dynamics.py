@@ -209,3 +209,23 @@ def test_small_A_diverges_for_cs_at_0p7():
     f = O.init_equilibrium(I.droplet_density(64, 64, 15, rl, rg))
     with pytest.raises(O.OracleUnstable):
         O.step(p, f, 50)
+
+
+@pytest.mark.parametrize("rho0,nu_expect", [(1.0, 0.2), (3.0, 0.125), (6.0, 0.05), (0.5, 0.2)])
+def test_density_dependent_viscosity_sets_the_shear_decay(rho0, nu_expect):
+    """Section 4.2's density-dependent viscosity (linear in rho between the
+    gas (1, 0.2) and liquid (5, 0.05) states, clamped): a shear wave in a
+    uniform fluid of density rho0 decays with nu(rho0)."""
+    L, U0 = 64, 1e-5
+    y = np.arange(L)
+    ux = np.broadcast_to((U0 * np.sin(2 * math.pi * y / L))[:, None], (L, 4)).copy()
+    p = O.Params(G=0.0, s=[1, 1.1, 1.1, 1, 1.1, 1, 1.1, 1.0, 1.0], var_visc=True, nu_g=0.2, nu_l=0.05,
+                 visc_rho_g=1.0, visc_rho_l=5.0)
+    f = O.init_equilibrium(np.full((L, 4), rho0), ux, np.zeros_like(ux))
+    O.step(p, f, 50)
+    a1 = O.macro(p, f)[1][:, 0] @ np.sin(2 * math.pi * y / L)
+    O.step(p, f, 300)
+    a2 = O.macro(p, f)[1][:, 0] @ np.sin(2 * math.pi * y / L)
+    k = 2 * math.pi / L
+    nu_meas = -math.log(a2 / a1) / (k * k * 300)
+    assert abs(nu_meas / nu_expect - 1) < 3e-3
