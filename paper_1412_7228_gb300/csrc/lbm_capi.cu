@@ -372,7 +372,10 @@ template <typename T> void fill_phys(lbm::Phys<T>& P, const HostParams& hp) {
     for (int k = 0; k < 9; ++k) {
         P.s[k] = T(hp.s[k]);
         P.hs[k] = T(1.0 - 0.5 * hp.s[k]);
+        P.ns[k] = -P.s[k];
+        P.nhs[k] = -P.hs[k];
     }
+    P.h2s7 = T(2) * P.hs[7];
     P.c1 = T(1.5 * hp.s[1]);
     P.c2 = (hp.flags & LBM_FLAG_LI_EPS) ? T(-1.5 * hp.s[2]) : T(0);
     P.rho_ref = T(hp.rho_ref);

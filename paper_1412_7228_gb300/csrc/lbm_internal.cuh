@@ -48,6 +48,8 @@ template <typename T> struct Phys {
     T A, kappa, G, two_over_G;   // Eq. 9, Eq. 23, Eq. 10
     T s[9];             // Lambda
     T hs[9];            // 1 - s/2, the forcing weight of Eq. 5
+    T ns[9], nhs[9];    // -s, -hs
+    T h2s7;             // 2 hs[7] (exact)
     T c1, c2;           // C[1] = c1 tr Q, C[2] = c2 tr Q (Eq. 26)
     T rho_ref;          // deviation reference
     int interact;       // 0 when G == 0: no psi, F = Q = 0

@@ -63,9 +63,9 @@ template <typename T> __device__ __forceinline__ T rho_dev(const T (&f)[9]) {
 // launch path the autotuner may pick.
 //
 // Product rounded on its own: never fused into an FMA with a neighbouring
-// add.  Used where a mirror or the x<->y transpose swaps two product terms
-// (p1^2 + p3^2, rho u_x^2 + rho u_y^2, ...): fma(a, a, b*b) is not
-// symmetric in a and b, a sum of two rounded products is.
+// add.  Used where a mirror swaps two product terms (p1^2 - p3^2, ...):
+// fma(a, a, -b*b) is not antisymmetric in a and b, a difference of two
+// rounded products is.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
@@ -92,18 +92,19 @@ template <> struct Fast<double> {
     static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
 };
 
+
 // The parameters one node needs, copied into registers once per tile (the
 // descriptor lives in global memory, and the compiler may not keep values
 // read through it across the node loop's stores).
 // FP32 keeps them as values; FP64, bound by its FP64 pipe rather than by
 // issue slots, keeps references and spends its registers on occupancy.
 template <typename T, typename V> struct RegsOf {
-    V s1, s2, s4, s6, s7, s8, hs1, hs2, hs4, hs6, hs7, hs8, c1, c2, rho_ref;
+    V ns1, ns2, ns4, ns6, ns7, ns8, hs1, nhs2, nhs4, nhs6, h2s7, hs8, c1, c2, rho_ref;   // ns = -s, nhs = -hs
     int var_visc;
     V nu_g, dnu, visc_rho_g, visc_inv_drho;
     __device__ __forceinline__ explicit RegsOf(const Phys<T>& P)
-        : s1(P.s[1]), s2(P.s[2]), s4(P.s[4]), s6(P.s[6]), s7(P.s[7]), s8(P.s[8]), hs1(P.hs[1]),
-          hs2(P.hs[2]), hs4(P.hs[4]), hs6(P.hs[6]), hs7(P.hs[7]), hs8(P.hs[8]), c1(P.c1), c2(P.c2),
+        : ns1(P.ns[1]), ns2(P.ns[2]), ns4(P.ns[4]), ns6(P.ns[6]), ns7(P.ns[7]), ns8(P.ns[8]), hs1(P.hs[1]),
+          nhs2(P.nhs[2]), nhs4(P.nhs[4]), nhs6(P.nhs[6]), h2s7(P.h2s7), hs8(P.hs[8]), c1(P.c1), c2(P.c2),
           rho_ref(P.rho_ref), var_visc(P.var_visc), nu_g(P.nu_g), dnu(P.dnu), visc_rho_g(P.visc_rho_g),
           visc_inv_drho(P.visc_inv_drho) {}
 };
@@ -111,13 +112,15 @@ template <typename T> struct RegsSel { using type = RegsOf<T, const T&>; };
 template <> struct RegsSel<float> { using type = RegsOf<float, float>; };
 template <typename T> using Regs = typename RegsSel<T>::type;
 
-template <typename T>
-__device__ __forceinline__ void collide(const Regs<T>& P, const T (&f)[9], T Fx, T Fy, T Qxx, T Qyy,
-                                        T Qxy, T (&out)[9]) {
+// P: the relaxation constants (register copies for FP32, references into the
+// descriptor for FP64).
+template <typename T, typename RP>
+__device__ __forceinline__ void collide(const RP& P, const T (&f)[9], T Fx, T Fy, T Qxx, T Qyy, T Qxy,
+                                        T (&out)[9]) {
     const T Sa = (f[1] + f[3]) + (f[2] + f[4]);
     const T Sd = (f[5] + f[7]) + (f[6] + f[8]);
     const T rt = f[0] + Sa + Sd;                       // rho - rho_ref, as rho_dev()
-    const T rho = P.rho_ref + rt;
+    const T rho = T(P.rho_ref) + rt;
     const T inv = Fast<T>::rcp(rho);
     const T d13 = f[1] - f[3], d24 = f[2] - f[4];
     const T Dxd = (f[5] - f[7]) + (f[8] - f[6]);
@@ -129,34 +132,37 @@ __device__ __forceinline__ void collide(const Regs<T>& P, const T (&f)[9], T Fx,
     const T vF = mul_rn(ux, Fx) + mul_rn(uy, Fy);
     const T trQ = Qxx + Qyy;
 
-    const T m1 = T(2) * Sd - Sa - T(4) * f[0];
-    const T m2 = Sd - T(2) * Sa + T(4) * f[0];
-    const T m4 = Dxd - T(2) * d13;
-    const T m6 = Dyd - T(2) * d24;
+    // a product with a power of two is exact, so fma(2^k, x, y) rounds like
+    // the separate multiply and add it replaces: same bits, one instruction
+    const T m1 = fma(T(-4), f[0], fma(T(2), Sd, -Sa));
+    const T m2 = fma(T(4), f[0], fma(T(-2), Sa, Sd));
+    const T m4 = fma(T(-2), d13, Dxd);
+    const T m6 = fma(T(-2), d24, Dyd);
     const T m7 = (f[1] + f[3]) - (f[2] + f[4]);
     const T m8 = (f[5] + f[7]) - (f[6] + f[8]);
 
     const T e1 = fma(T(3), ru2, T(-2) * rt);          // m_eq deviations (Eq. 4)
     const T e2 = fma(T(-3), ru2, rt);
     const T vF6 = T(6) * vF;
-    const T ms1 = fma(P.c1, trQ, fma(P.hs1, vF6, fma(-P.s1, m1 - e1, m1)));
-    const T ms2 = fma(P.c2, trQ, fma(-P.hs2, vF6, fma(-P.s2, m2 - e2, m2)));
+    const T ms1 = fma(T(P.c1), trQ, fma(T(P.hs1), vF6, fma(T(P.ns1), m1 - e1, m1)));
+    const T ms2 = fma(T(P.c2), trQ, fma(T(P.nhs2), vF6, fma(T(P.ns2), m2 - e2, m2)));
     const T ms3 = jx + Fx;                             // = m3 - s_j (m3 - rho v_x) + (1 - s_j/2) F_x
-    const T ms4 = fma(-P.hs4, Fx, fma(-P.s4, m4 + rux, m4));
+    const T ms4 = fma(T(P.nhs4), Fx, fma(T(P.ns4), m4 + rux, m4));
     const T ms5 = jy + Fy;
-    const T ms6 = fma(-P.hs6, Fy, fma(-P.s6, m6 + ruy, m6));
+    const T ms6 = fma(T(P.nhs6), Fy, fma(T(P.ns6), m6 + ruy, m6));
     // shear rates: fixed, or from the density-dependent viscosity (Section 4.2)
-    T s7 = P.s7, s8 = P.s8, hs7 = P.hs7, hs8 = P.hs8;
+    T ns7 = T(P.ns7), ns8 = T(P.ns8), h2s7 = T(P.h2s7), hs8 = T(P.hs8);   // h2s7 = 2 hs7
     if (P.var_visc) {
-        const T w = fmin(fmax((rho - P.visc_rho_g) * P.visc_inv_drho, T(0)), T(1));
-        const T sn = Fast<T>::rcp(fma(T(3), fma(w, P.dnu, P.nu_g), T(0.5)));
-        s7 = s8 = sn;
-        hs7 = hs8 = fma(T(-0.5), sn, T(1));
+        const T w = fmin(fmax((rho - T(P.visc_rho_g)) * T(P.visc_inv_drho), T(0)), T(1));
+        const T sn = Fast<T>::rcp(fma(T(3), fma(w, T(P.dnu), T(P.nu_g)), T(0.5)));
+        ns7 = ns8 = -sn;
+        hs8 = fma(T(-0.5), sn, T(1));
+        h2s7 = T(2) - sn;                                 // = 2 hs8 exactly
     }
-    const T ms7 = fma(-s7, Qxx - Qyy,
-                      fma(hs7, T(2) * (mul_rn(ux, Fx) - mul_rn(uy, Fy)),
-                          fma(-s7, m7 - (mul_rn(rux, ux) - mul_rn(ruy, uy)), m7)));
-    const T ms8 = fma(-s8, Qxy, fma(hs8, mul_rn(ux, Fy) + mul_rn(uy, Fx), fma(-s8, m8 - rux * uy, m8)));
+    const T ms7 = fma(ns7, Qxx - Qyy,
+                      fma(h2s7, mul_rn(ux, Fx) - mul_rn(uy, Fy),
+                          fma(ns7, m7 - (mul_rn(rux, ux) - mul_rn(ruy, uy)), m7)));
+    const T ms8 = fma(ns8, Qxy, fma(hs8, mul_rn(ux, Fy) + mul_rn(uy, Fx), fma(ns8, m8 - mul_rn(rux, uy), m8)));
 
     // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
     // The rows of a1..a8 sum to zero over the nine outputs, so the mass of the
@@ -165,24 +171,24 @@ __device__ __forceinline__ void collide(const Regs<T>& P, const T (&f)[9], T Fx,
     // bias to the mass at every step of a steady state.
     const T c9 = T(1.0 / 9.0);
     const T q9 = rt * c9;
-    const T a0 = fma(fma(-q9, T(9), rt), c9, q9);
-    const T a1 = ms1 * T(1.0 / 36.0), a2 = ms2 * T(1.0 / 36.0);
-    const T a3 = ms3 * T(1.0 / 6.0), a4 = ms4 * T(1.0 / 12.0);
-    const T a5 = ms5 * T(1.0 / 6.0), a6 = ms6 * T(1.0 / 12.0);
-    const T a7 = ms7 * T(0.25), a8 = ms8 * T(0.25);
-    const T bax = a0 - a1 - T(2) * a2;
-    const T bdg = a0 + T(2) * a1 + a2;
-    const T X = a3 - T(2) * a4, Y = a5 - T(2) * a6;
+    const T a0 = fma(fma(q9, T(-9), rt), c9, q9);
+    const T a1 = mul_rn(ms1, T(1.0 / 36.0)), a2 = mul_rn(ms2, T(1.0 / 36.0));
+    const T a3 = mul_rn(ms3, T(1.0 / 6.0)), a4 = mul_rn(ms4, T(1.0 / 12.0));
+    const T a5 = mul_rn(ms5, T(1.0 / 6.0)), a6 = mul_rn(ms6, T(1.0 / 12.0));
+    // a7 = ms7 / 4 and a8 = ms8 / 4 are exact: folded into the last add
+    const T bax = fma(T(-2), a2, a0 - a1);
+    const T bdg = fma(T(2), a1, a0) + a2;
+    const T X = fma(T(-2), a4, a3), Y = fma(T(-2), a6, a5);
     const T DX = a3 + a4, DY = a5 + a6;
-    out[0] = a0 - T(4) * a1 + T(4) * a2;
-    out[1] = bax + X + a7;
-    out[2] = bax + Y - a7;
-    out[3] = bax - X + a7;
-    out[4] = bax - Y - a7;
-    out[5] = bdg + DX + DY + a8;
-    out[6] = bdg - DX + DY - a8;
-    out[7] = bdg - DX - DY + a8;
-    out[8] = bdg + DX - DY - a8;
+    out[0] = fma(T(4), a2, fma(T(-4), a1, a0));
+    out[1] = fma(T(0.25), ms7, bax + X);
+    out[2] = fma(T(-0.25), ms7, bax + Y);
+    out[3] = fma(T(0.25), ms7, bax - X);
+    out[4] = fma(T(-0.25), ms7, bax - Y);
+    out[5] = fma(T(0.25), ms8, bdg + DX + DY);
+    out[6] = fma(T(-0.25), ms8, bdg - DX + DY);
+    out[7] = fma(T(0.25), ms8, bdg - DX - DY);
+    out[8] = fma(T(-0.25), ms8, bdg + DX - DY);
 }
 
 // Equation-of-state constants in registers.
@@ -212,6 +218,37 @@ template <typename T> __device__ __forceinline__ T radicand_step(const EosRegs<T
     return P.two_over_G * fma(rho, T(-1.0 / 3.0), p);
 }
 
+// Hybrid force (Eq. 9) and modifying tensor (Eq. 23, x G/2) of one node
+// from psi at the node (p0) and its eight neighbours (p_a at x + e_a).
+// negG = -G, hA = A/2, omA = 1 - A, kG2 = kappa G / 2.
+template <typename T>
+__device__ __forceinline__ void force_q(T negG, T hA, T omA, T kG2, T p0, T p1, T p2, T p3, T p4, T p5, T p6,
+                                        T p7, T p8, T& Fx, T& Fy, T& Qxx, T& Qyy, T& Qxy) {
+    const T w1 = T(1.0 / 3.0), w2 = T(1.0 / 12.0);
+    const T q1 = mul_rn(p1, p1), q2 = mul_rn(p2, p2), q3 = mul_rn(p3, p3), q4 = mul_rn(p4, p4);
+    const T q5 = mul_rn(p5, p5), q6 = mul_rn(p6, p6), q7 = mul_rn(p7, p7), q8 = mul_rn(p8, p8);
+    // Eq. 9: F = -G [ (A/2) sum w psi_n^2 e + (1-A) psi sum w psi_n e ]
+    const T gx1 = fma(w1, p1 - p3, w2 * ((p5 - p7) + (p8 - p6)));
+    const T gy1 = fma(w1, p2 - p4, w2 * ((p5 - p7) + (p6 - p8)));
+    const T gx2 = fma(w1, q1 - q3, w2 * ((q5 - q7) + (q8 - q6)));
+    const T gy2 = fma(w1, q2 - q4, w2 * ((q5 - q7) + (q6 - q8)));
+    const T c = omA * p0;
+    Fx = negG * fma(c, gx1, hA * gx2);
+    Fy = negG * fma(c, gy1, hA * gy2);
+    // Eq. 23 (x G/2): sums of w (psi_n - psi) e e and w (psi_n^2 - psi^2) e e;
+    // sum w e_x^2 = sum w e_y^2 = 1 and sum w e_x e_y = 0 over the ring
+    const T d1 = w2 * ((p5 + p7) + (p6 + p8));
+    const T d2 = w2 * ((q5 + q7) + (q6 + q8));
+    const T q0 = mul_rn(p0, p0);
+    const T sxx1 = fma(w1, p1 + p3, d1) - p0, syy1 = fma(w1, p2 + p4, d1) - p0;
+    const T sxy1 = w2 * ((p5 + p7) - (p6 + p8));
+    const T sxx2 = fma(w1, q1 + q3, d2) - q0, syy2 = fma(w1, q2 + q4, d2) - q0;
+    const T sxy2 = w2 * ((q5 + q7) - (q6 + q8));
+    Qxx = kG2 * fma(c, sxx1, hA * sxx2);
+    Qyy = kG2 * fma(c, syy1, hA * syy2);
+    Qxy = kG2 * fma(c, sxy1, hA * sxy2);
+}
+
 // One kernel, two ways to find the work: ONE = a single lattice whose
 // constants and tensor maps arrive in the __grid_constant__ argument, tile
 // coordinates from the tile index; otherwise a tile table over instances
@@ -219,9 +256,8 @@ template <typename T> __device__ __forceinline__ T radicand_step(const EosRegs<T
 // persistent with a two-stage TMA pipeline: while tile k is collided, the
 // box of tile k+1 streams into the other shared-memory buffer.
 template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
-__global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, const int4* __restrict__ tiles,
-                                             int ntiles, int parity, unsigned long long timeout_ns,
-                                             const __grid_constant__ StepArgs<T> one) {
+__device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const int4* __restrict__ tiles, int ntiles,
+                                          int parity, unsigned long long timeout_ns, const StepArgs<T>& one) {
     using Gm = Geom<T, BX, BY, NT, NBUF>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -263,7 +299,6 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
     };
     if (tid == 0) issue(t, 0);
 
-    constexpr T w1 = T(1.0 / 3.0), w2 = T(1.0 / 12.0);
 #pragma unroll 1
     for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
         const int b = NBUF == 2 ? (k & 1) : 0;
@@ -278,8 +313,7 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
         int* status = ONE ? one.status : I->status;
         const int interact = P.interact;
         const EosRegs<T> E(P);
-        const Regs<T> R(P);
-        const T rho_ref = R.rho_ref;
+        const T rho_ref = P.rho_ref;
         bool bad = false;
 
         bool ok = mbar_wait_bounded(&bar[b], ph, timeout_ns);
@@ -316,15 +350,33 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
         if (NBUF == 2 && tid == 0 && t + static_cast<int>(gridDim.x) < ntiles) issue(t + gridDim.x, b ^ 1);
 
         // ---- collide and stream every owned node -------------------------
-        // each thread owns ROWS consecutive rows of one column; the 3x3 psi
-        // neighbourhood slides down with it (three new loads per node)
         T* __restrict__ dst = static_cast<T*>(ONE ? one.pop[parity ^ 1] : I->pop[parity ^ 1]);
         const long long plane = ONE ? one.plane : I->plane;
         const int pitch = ONE ? one.pitch : I->pitch;
-        const T G = P.G, A = P.A;
-        const T hA = T(0.5) * A, omA = T(1) - A;
-        const T kG2 = P.kappa * G * T(0.5);
         const bool border = x0 < 2 || x0 + BX > nx - 2 || y0 < 2 || y0 + BY > ny - 2;
+        // periodic images in the ghost cells read by the neighbouring tiles
+        auto ghost = [&](T* o, int x, int y, const T (&v)[9]) {
+            const bool xl = x < 2, xr = x >= nx - 2, yl = y < 2, yr = y >= ny - 2;
+            if (!(xl || xr || yl || yr)) return;
+            const int oxs[3] = {0, xl ? nx : 0, xr ? -nx : 0};
+            const int oys[3] = {0, yl ? ny : 0, yr ? -ny : 0};
+            const bool hx[3] = {true, xl, xr};
+            const bool hy[3] = {true, yl, yr};
+            for (int iy = 0; iy < 3; ++iy)
+                for (int ix = 0; ix < 3; ++ix) {
+                    if (!(hx[ix] && hy[iy]) || (ix == 0 && iy == 0)) continue;
+                    T* g = o + static_cast<long long>(oys[iy]) * pitch + oxs[ix];
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) g[a * plane] = v[a];
+                }
+        };
+
+        // each thread owns ROWS consecutive rows of one column; the 3x3 psi
+        // neighbourhood slides down with it (three new loads per node)
+        const Regs<T> R(P);
+        const T G = P.G, A = P.A;
+        const T negG = -G, hA = T(0.5) * A, omA = T(1) - A;
+        const T kG2 = P.kappa * G * T(0.5);
         const int ly0 = ty * Gm::ROWS;
         const T* s0 = sp + (ly0 + 1) * Gm::WP + (tx + 1);   // psi of node (tx, ly0)
         T wm0 = T(0), wm1 = T(0), wm2 = T(0), w00 = T(0), w01 = T(0), w02 = T(0);
@@ -355,59 +407,18 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
                 for (int a = 0; a < 9; ++a) f[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
 
                 T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
-                if (interact) {
-                    const T p0 = w01;
-                    const T p1 = w02, p2 = wp1, p3 = w00, p4 = wm1;
-                    const T p5 = wp2, p6 = wp0, p7 = wm0, p8 = wm2;
-                    const T q1 = mul_rn(p1, p1), q2 = mul_rn(p2, p2), q3 = mul_rn(p3, p3), q4 = mul_rn(p4, p4);
-                    const T q5 = mul_rn(p5, p5), q6 = mul_rn(p6, p6), q7 = mul_rn(p7, p7), q8 = mul_rn(p8, p8);
-                    // Eq. 9: F = -G [ (A/2) sum w psi_n^2 e + (1-A) psi sum w psi_n e ]
-                    const T gx1 = fma(w1, p1 - p3, w2 * ((p5 - p7) + (p8 - p6)));
-                    const T gy1 = fma(w1, p2 - p4, w2 * ((p5 - p7) + (p6 - p8)));
-                    const T gx2 = fma(w1, q1 - q3, w2 * ((q5 - q7) + (q8 - q6)));
-                    const T gy2 = fma(w1, q2 - q4, w2 * ((q5 - q7) + (q6 - q8)));
-                    const T c = omA * p0;
-                    Fx = -G * fma(c, gx1, hA * gx2);
-                    Fy = -G * fma(c, gy1, hA * gy2);
-                    // Eq. 23 (x G/2): sums of w (psi_n - psi) e e and w (psi_n^2 - psi^2) e e;
-                    // sum w e_x^2 = sum w e_y^2 = 1 and sum w e_x e_y = 0 over the ring
-                    const T d1 = w2 * ((p5 + p7) + (p6 + p8));
-                    const T d2 = w2 * ((q5 + q7) + (q6 + q8));
-                    const T q0 = mul_rn(p0, p0);
-                    const T sxx1 = fma(w1, p1 + p3, d1) - p0, syy1 = fma(w1, p2 + p4, d1) - p0;
-                    const T sxy1 = w2 * ((p5 + p7) - (p6 + p8));
-                    const T sxx2 = fma(w1, q1 + q3, d2) - q0, syy2 = fma(w1, q2 + q4, d2) - q0;
-                    const T sxy2 = w2 * ((q5 + q7) - (q6 + q8));
-                    Qxx = kG2 * fma(c, sxx1, hA * sxx2);
-                    Qyy = kG2 * fma(c, syy1, hA * syy2);
-                    Qxy = kG2 * fma(c, sxy1, hA * sxy2);
-                }
+                if (interact)
+                    force_q<T>(negG, hA, omA, kG2, w01, w02, wp1, w00, wm1, wp2, wp0, wm0, wm2, Fx, Fy, Qxx, Qyy,
+                               Qxy);
 
                 T out[9];
-                collide(R, f, Fx, Fy, Qxx, Qyy, Qxy, out);
+                collide<T>(R, f, Fx, Fy, Qxx, Qyy, Qxy, out);
                 if (!(out[0] == out[0])) bad = true;
 
                 T* o = dst + static_cast<long long>(y + GY) * pitch + (x + Gm::GX);
 #pragma unroll
                 for (int a = 0; a < 9; ++a) o[a * plane] = out[a];
-
-                // periodic images in the ghost cells read by the neighbouring tiles
-                if (border) {
-                    const bool xl = x < 2, xr = x >= nx - 2, yl = y < 2, yr = y >= ny - 2;
-                    if (xl || xr || yl || yr) {
-                        const int oxs[3] = {0, xl ? nx : 0, xr ? -nx : 0};
-                        const int oys[3] = {0, yl ? ny : 0, yr ? -ny : 0};
-                        const bool hx[3] = {true, xl, xr};
-                        const bool hy[3] = {true, yl, yr};
-                        for (int iy = 0; iy < 3; ++iy)
-                            for (int ix = 0; ix < 3; ++ix) {
-                                if (!(hx[ix] && hy[iy]) || (ix == 0 && iy == 0)) continue;
-                                T* g = o + static_cast<long long>(oys[iy]) * pitch + oxs[ix];
-#pragma unroll
-                                for (int a = 0; a < 9; ++a) g[a * plane] = out[a];
-                            }
-                    }
-                }
+                if (border) ghost(o, x, y, out);
             }
             wm0 = w00; wm1 = w01; wm2 = w02;
             w00 = wp0; w01 = wp1; w02 = wp2;
@@ -416,6 +427,30 @@ __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, con
     }
 }
 
+// The kernels.  FP32 single-lattice launches ask for 1024 resident threads
+// per SM (two CTAs of 512), which caps their registers at 64; the others
+// leave the register count to the compiler.
+template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
+__global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, const int4* __restrict__ tiles,
+                                             int ntiles, int parity, unsigned long long timeout_ns,
+                                             const __grid_constant__ StepArgs<T> one) {
+    step_body<T, BX, BY, NT, NBUF, ONE>(insts, tiles, ntiles, parity, timeout_ns, one);
+}
+template <int BX, int BY, int NT, int NBUF>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_step_f32(const Inst* __restrict__ insts,
+                                                            const int4* __restrict__ tiles, int ntiles, int parity,
+                                                            unsigned long long timeout_ns,
+                                                            const __grid_constant__ StepArgs<float> one) {
+    step_body<float, BX, BY, NT, NBUF, true>(insts, tiles, ntiles, parity, timeout_ns, one);
+}
+// the kernel a (precision, ONE) launch uses
+template <typename T, int BX, int BY, int NT, int NBUF, bool ONE> struct KSel {
+    static constexpr auto fn = &k_step<T, BX, BY, NT, NBUF, ONE>;
+};
+template <int BX, int BY, int NT, int NBUF> struct KSel<float, BX, BY, NT, NBUF, true> {
+    static constexpr auto fn = &k_step_f32<BX, BY, NT, NBUF>;
+};
+
 // ---- tile configurations ------------------------------------------------
 template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
     using Gm = Geom<T, BX, BY, NT, NBUF>;
@@ -423,13 +458,13 @@ template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
     static TileCfg tc() { return TileCfg{BX, BY, NT, NBUF}; }
     static size_t smem() { return Gm::smem; }
     template <bool ONE> static cudaError_t prep_one() {
-        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, NT, NBUF, ONE>,
+        cudaError_t e = cudaFuncSetAttribute(KSel<T, BX, BY, NT, NBUF, ONE>::fn,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(Gm::smem));
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, occ = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<T, BX, BY, NT, NBUF, ONE>, NT,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, KSel<T, BX, BY, NT, NBUF, ONE>::fn, NT,
                                                                 Gm::smem)) != cudaSuccess)
             return e;
         grid_cap[ONE ? 1 : 0] = (occ > 0 ? occ : 1) * sms;
@@ -445,11 +480,11 @@ template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
         const int cap = grid_cap[one ? 1 : 0];
         const int grid = NBUF == 1 ? n : (n < cap ? n : cap);
         if (one) {
-            k_step<T, BX, BY, NT, NBUF, true><<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to,
-                                                                          *static_cast<const StepArgs<T>*>(one));
+            KSel<T, BX, BY, NT, NBUF, true>::fn<<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to,
+                                                                            *static_cast<const StepArgs<T>*>(one));
         } else {
             static const StepArgs<T> none{};
-            k_step<T, BX, BY, NT, NBUF, false><<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to, none);
+            KSel<T, BX, BY, NT, NBUF, false>::fn<<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to, none);
         }
         return cudaGetLastError();
     }
