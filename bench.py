@@ -303,7 +303,8 @@ def run_ours(args):
     traffic = kernel_traffic(args.precision)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": bpu,
-            "kernel": "lbm::k_step<%s,%d,%d,%d,%d>" % ((("float",) if prec == P.LBM_FP32 else ("double",)) + tuple(tile))}
+            "kernel": ("lbm::k_step_f32<%d,%d,%d,%d>" % tuple(tile)) if prec == P.LBM_FP32
+                      else ("lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(tile))}
     lat.close()
 
     # ---- FP64 on the same workload (fewer steps: it is FP64-ALU bound) ----
@@ -320,7 +321,7 @@ def run_ours(args):
         m64 = N * k64 / t64 / 1e6
         fp64 = {"value": m64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1000.0,
                 "hbm_frac": 144 * N / (t64 / k64) / 1e9 / peak, "bytes_per_update": 144,
-                "kernel": "lbm::k_step<double,%d,%d,%d,%d>" % tuple(P.lbm_tile_configs(P.LBM_FP64)[1])}
+                "kernel": "lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(P.lbm_tile_configs(P.LBM_FP64)[1])}
         alu = fp64_alu_roofline(m64)
         if alu:
             fp64["roofline"] = alu
