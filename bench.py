@@ -82,9 +82,11 @@ def measured_peak():
         return PEAK_FALLBACK_GBS, "fallback"
 
 
-def kernel_traffic(prec_name):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged."""
+def kernel_traffic(prec_name, kernel):
+    """Measured DRAM bytes per lattice update of the step kernel from the
+    committed ncu summary, valid only for the kernel it names and while the
+    kernel source is unchanged (traffic per node does not depend on the
+    domain size once the arrays exceed L2)."""
     src = os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", "lbm_step.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "step_%s_4096_traffic.txt" % prec_name)
@@ -92,10 +94,10 @@ def kernel_traffic(prec_name):
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
     except OSError:
         return None
-    if kv.get("lbm_step_cu_sha256_16") != sha:
+    if kv.get("lbm_step_cu_sha256_16") != sha or kv.get("kernel") != kernel:
         return None
     try:
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv["bytes_per_update"])
     except (KeyError, ValueError):
         return None
 
@@ -300,11 +302,15 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     bpu = 72 if prec == P.LBM_FP32 else 144
     achieved = bpu * N / avg_launch / 1e9
-    traffic = kernel_traffic(args.precision)
+    kname = (("lbm::k_step_f32<%d,%d,%d,%d>" % tuple(tile)) if prec == P.LBM_FP32
+             else ("lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(tile)))
+    tpu = kernel_traffic(args.precision, kname)
+    traffic = tpu * N if tpu is not None else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": bpu,
-            "kernel": ("lbm::k_step_f32<%d,%d,%d,%d>" % tuple(tile)) if prec == P.LBM_FP32
-                      else ("lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(tile))}
+            "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": bpu, "kernel": kname}
+    if traffic is not None:
+        roof["traffic_bytes_per_update"] = tpu
+        roof["traffic_gbs"] = traffic / avg_launch / 1e9
     lat.close()
 
     # ---- FP64 on the same workload (fewer steps: it is FP64-ALU bound) ----

@@ -59,3 +59,21 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         steps, warmup, nx, ny = 3, 3, 4096, 4096
     assert bench.run_reference(A) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_figure_is_used_only_for_the_profiled_kernel():
+    """The committed ncu traffic applies to the kernel it names and only while
+    the kernel source hashes to the value recorded beside it."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", "lbm_step.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "step_fp32_4096_traffic.txt")
+    kv = dict(l.strip().split("=", 1) for l in open(path) if "=" in l and not l.startswith("#"))
+    got = bench.kernel_traffic("fp32", kv["kernel"])
+    if kv["lbm_step_cu_sha256_16"] == sha:
+        assert got == float(kv["bytes_per_update"]) and 72.0 <= got < 80.0
+    else:
+        assert got is None
+    assert bench.kernel_traffic("fp32", "lbm::some_other_kernel") is None
