@@ -1,0 +1,146 @@
+"""Argument checks, allocation failure and a lattice whose population arrays
+exceed 2^31 elements, on the GPU.  Every rejected call returns its error code,
+creates nothing, and leaves an existing context usable."""
+import ctypes
+import warnings
+
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+import oracle as O
+
+warnings.filterwarnings("ignore", category=Warning, module="scipy")
+
+pytestmark = pytest.mark.gpu
+S_CFG = [1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0]
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1412_7228_gb300 as P
+    return P
+
+
+def _cs(P):
+    eos = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
+    _, Tc, _ = P.lbm_eos_critical(eos)
+    eos.T = 0.7 * Tc
+    op = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, T=eos.T, A=-0.85, kappa=0.3, s=list(S_CFG))
+    rg, rl, _ = P.lbm_eos_maxwell(eos)
+    return eos, op, rg, rl
+
+
+def _create(P, nx, ny, prec, buf=None, nbytes=0):
+    ctx = ctypes.c_void_p()
+    rc = P.lbm.lib().lbm_create(ctypes.byref(ctx), nx, ny, prec, buf, nbytes, None)
+    return rc, ctx
+
+
+def test_shapes_and_precisions_are_checked(P):
+    for nx, ny, prec in ((1, 8, 1), (8, 1, 1), (0, 0, 1), (-4, 8, 1), ((1 << 20) + 1, 8, 1), (8, 8, 3), (8, 8, 0)):
+        rc, ctx = _create(P, nx, ny, prec)
+        assert rc == P.lbm.LBM_EINVAL and not ctx.value, (nx, ny, prec)
+
+
+def test_allocation_failure_is_an_error_code(P):
+    """2^20 x 2^20 nodes need about 80 TB: the allocation fails cleanly."""
+    rc, ctx = _create(P, 1 << 20, 1 << 20, P.LBM_FP32)
+    assert rc == P.lbm.LBM_ENOMEM and not ctx.value
+
+
+def test_caller_buffer_is_checked(P):
+    import torch
+    need = P.lbm_required_bytes(64, 64, P.LBM_FP32)
+    buf = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr()
+    rc, ctx = _create(P, 64, 64, P.LBM_FP32, ctypes.c_void_p(base), need - 256)
+    assert rc == P.lbm.LBM_ENOMEM and not ctx.value
+    rc, ctx = _create(P, 64, 64, P.LBM_FP32, ctypes.c_void_p(base + 16), need)
+    assert rc == P.lbm.LBM_EINVAL and not ctx.value
+    rc, ctx = _create(P, 64, 64, P.LBM_FP32, ctypes.c_void_p(base), need)
+    assert rc == P.lbm.LBM_OK and ctx.value
+    P.lbm.lib().lbm_destroy(ctx)
+
+
+def test_rejected_calls_leave_the_context_usable(P):
+    eos, op, rg, rl = _cs(P)
+    lat = P.Lattice(40, 36, P.LBM_FP32)
+    with pytest.raises(P.LbmError) as ei:
+        lat.step(1)                                   # parameters never set
+    assert ei.value.code == P.lbm.LBM_EINVAL
+    bad = [dict(s=[1.0] * 8 + [2.0]), dict(s=[0.0] + [1.0] * 8), dict(s=[1.0] * 8 + [float("nan")])]
+    for kw in bad:
+        with pytest.raises(P.LbmError) as ei:
+            lat.set_params(eos, -0.85, 0.3, rho_ref=rg, **kw)
+        assert ei.value.code == P.lbm.LBM_EINVAL
+    cold = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, T=0.0)
+    with pytest.raises(P.LbmError):
+        lat.set_params(cold, -0.85, 0.3, rho_ref=rg)
+    with pytest.raises(P.LbmError):
+        lat.set_params(eos, float("inf"), 0.3, rho_ref=rg)
+    rc = P.lbm.lib().lbm_step(lat.ctx, -1)
+    assert rc == P.lbm.LBM_EINVAL
+    rc = P.lbm.lib().lbm_set_schedule(lat.ctx, 99, 0)
+    assert rc == P.lbm.LBM_EINVAL
+
+    rho0 = I.droplet_density(40, 36, 9, rl, rg)
+    lat.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=rg)
+    lat.init_density(rho0)
+    with pytest.raises(P.LbmError):
+        lat.measure_pressure_jump(20.0, 18.0, -1.0, 14.0)
+    lat.step(20)
+    got = lat.read_fields(which=("rho",))["rho"]
+    lat.close()
+    f = O.init_equilibrium(rho0)
+    O.step(op, f, 20)
+    ref = O.macro(op, f)[0]
+    assert np.abs(got - ref).max() <= 2e-5 * ref.max()
+
+
+def test_batch_index_is_checked(P):
+    eos, op, rg, rl = _cs(P)
+    b = P.Batch([32, 48], [32, 40], P.LBM_FP32)
+    for i in (-1, 2):
+        with pytest.raises(P.LbmError) as ei:
+            b.set_params(i, eos, -0.85, 0.3, rho_ref=rg)
+        assert ei.value.code == P.lbm.LBM_EINVAL
+    b.close()
+
+
+def test_lattice_with_more_than_2_31_population_elements(P):
+    """16384^2 spinodal in FP32: 9 x 16392 x 16388 = 2.4e9 elements per time
+    level, so every plane offset past the first overflows 32 bits.  3 steps,
+    then oracle windows (mirror-extended, as in the full-size tests) at the
+    far corner, the last plane rows and seeded places, and the mass."""
+    eos, op, rg, rl = _cs(P)
+    n, steps, W, M = 16384, 3, 24, 6
+    rho0 = I.spinodal_density(n, n, 0.25, 0.01, 14127228)
+    lat = P.Lattice(n, n, P.LBM_FP32)
+    lat.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=0.25)
+    lat.init_density(rho0)
+    m0 = lat.stats()["mass"]
+    lat.use_graphs(True)
+    lat.step(steps)
+    m1 = lat.stats()["mass"]
+    rho = lat.read_fields(which=("rho",))["rho"]
+    lat.close()
+    assert abs(m1 / m0 - 1) < 1e-7
+    rng = np.random.default_rng(16384)
+    pts = [(n - 1, n - 1), (n // 2, n - 3), (n - 130, 5)] + [tuple(int(v) for v in rng.integers(0, n, 2))
+                                                              for _ in range(3)]
+    worst = 0.0
+    for cx, cy in pts:
+        ix = (np.arange(W) + cx - W // 2) % n
+        iy = (np.arange(W) + cy - W // 2) % n
+        w = rho0[np.ix_(iy, ix)]
+        top = np.concatenate([w, w[:, ::-1]], axis=1)
+        f = O.init_equilibrium(np.ascontiguousarray(np.concatenate([top, top[::-1, :]], axis=0)))
+        O.step(op, f, steps)
+        ref = O.macro(op, f)[0][:W, :W][M:W - M, M:W - M]
+        got = rho[np.ix_(iy, ix)][M:W - M, M:W - M]
+        worst = max(worst, float(np.abs(got / ref - 1).max()))
+    assert worst <= 1e-6, worst
