@@ -32,6 +32,9 @@ METRIC = "MLUPS and % of HBM roofline, FP32 vs FP64 on one GB300, sigma err <= 1
 SEED = 14127228
 S_CFG = [1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0]
 A_CFG, KAPPA_CFG, TR_CFG, RHO0 = -0.85, 0.3, 0.7, 0.25
+# default tile configurations (indices into lbm_tile_config): the fastest at
+# 4096^2 when timed with lbm_autotune, 128 x 16 (FP32) and 64 x 16 (FP64)
+TILE_FP32, TILE_FP64 = 0, 5
 PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -271,7 +274,7 @@ def run_ours(args):
     if args.autotune:
         k, s, ms = lat.autotune(10)
     else:
-        k = args.tile if args.tile is not None else (0 if prec == P.LBM_FP32 else 1)
+        k = args.tile if args.tile is not None else (TILE_FP32 if prec == P.LBM_FP32 else TILE_FP64)
         lat.set_schedule(k, 0)
     tile = P.lbm_tile_configs(prec)[k]
     lat.use_graphs(True)
@@ -317,7 +320,7 @@ def run_ours(args):
     fp64 = None
     if not args.no_fp64 and prec == P.LBM_FP32:
         lat64 = make_lattice(P, nx, ny, P.LBM_FP64, rho0)
-        lat64.set_schedule(1, 0)
+        lat64.set_schedule(TILE_FP64, 0)
         lat64.use_graphs(True)
         lat64.step(min(args.warmup, 10))
         lat64.sync()
@@ -327,7 +330,7 @@ def run_ours(args):
         m64 = N * k64 / t64 / 1e6
         fp64 = {"value": m64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1000.0,
                 "hbm_frac": 144 * N / (t64 / k64) / 1e9 / peak, "bytes_per_update": 144,
-                "kernel": "lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(P.lbm_tile_configs(P.LBM_FP64)[1])}
+                "kernel": "lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(P.lbm_tile_configs(P.LBM_FP64)[TILE_FP64])}
         alu = fp64_alu_roofline(m64)
         if alu:
             fp64["roofline"] = alu

@@ -376,6 +376,8 @@ template <typename T> void fill_phys(lbm::Phys<T>& P, const HostParams& hp) {
         P.nhs[k] = -P.hs[k];
     }
     P.h2s7 = T(2) * P.hs[7];
+    P.h6s1 = T(6.0 * (1.0 - 0.5 * hp.s[1]));
+    P.nh6s2 = T(-6.0 * (1.0 - 0.5 * hp.s[2]));
     P.c1 = T(1.5 * hp.s[1]);
     P.c2 = (hp.flags & LBM_FLAG_LI_EPS) ? T(-1.5 * hp.s[2]) : T(0);
     P.rho_ref = T(hp.rho_ref);

@@ -50,6 +50,7 @@ template <typename T> struct Phys {
     T hs[9];            // 1 - s/2, the forcing weight of Eq. 5
     T ns[9], nhs[9];    // -s, -hs
     T h2s7;             // 2 hs[7] (exact)
+    T h6s1, nh6s2;      // 6 hs[1], -6 hs[2]: the forcing weights of S[1] = 6 v.F, S[2] = -6 v.F
     T c1, c2;           // C[1] = c1 tr Q, C[2] = c2 tr Q (Eq. 26)
     T rho_ref;          // deviation reference
     int interact;       // 0 when G == 0: no psi, F = Q = 0

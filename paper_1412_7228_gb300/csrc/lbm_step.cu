@@ -99,12 +99,12 @@ template <> struct Fast<double> {
 // FP32 keeps them as values; FP64, bound by its FP64 pipe rather than by
 // issue slots, keeps references and spends its registers on occupancy.
 template <typename T, typename V> struct RegsOf {
-    V ns1, ns2, ns4, ns6, ns7, ns8, hs1, nhs2, nhs4, nhs6, h2s7, hs8, c1, c2, rho_ref;   // ns = -s, nhs = -hs
+    V ns1, ns2, ns4, ns6, ns7, ns8, h6s1, nh6s2, nhs4, nhs6, h2s7, hs8, c1, c2, rho_ref;   // ns = -s, nhs = -hs
     int var_visc;
     V nu_g, dnu, visc_rho_g, visc_inv_drho;
     __device__ __forceinline__ explicit RegsOf(const Phys<T>& P)
-        : ns1(P.ns[1]), ns2(P.ns[2]), ns4(P.ns[4]), ns6(P.ns[6]), ns7(P.ns[7]), ns8(P.ns[8]), hs1(P.hs[1]),
-          nhs2(P.nhs[2]), nhs4(P.nhs[4]), nhs6(P.nhs[6]), h2s7(P.h2s7), hs8(P.hs[8]), c1(P.c1), c2(P.c2),
+        : ns1(P.ns[1]), ns2(P.ns[2]), ns4(P.ns[4]), ns6(P.ns[6]), ns7(P.ns[7]), ns8(P.ns[8]), h6s1(P.h6s1),
+          nh6s2(P.nh6s2), nhs4(P.nhs[4]), nhs6(P.nhs[6]), h2s7(P.h2s7), hs8(P.hs[8]), c1(P.c1), c2(P.c2),
           rho_ref(P.rho_ref), var_visc(P.var_visc), nu_g(P.nu_g), dnu(P.dnu), visc_rho_g(P.visc_rho_g),
           visc_inv_drho(P.visc_inv_drho) {}
 };
@@ -141,11 +141,12 @@ __device__ __forceinline__ void collide(const RP& P, const T (&f)[9], T Fx, T Fy
     const T m7 = (f[1] + f[3]) - (f[2] + f[4]);
     const T m8 = (f[5] + f[7]) - (f[6] + f[8]);
 
-    const T e1 = fma(T(3), ru2, T(-2) * rt);          // m_eq deviations (Eq. 4)
-    const T e2 = fma(T(-3), ru2, rt);
-    const T vF6 = T(6) * vF;
-    const T ms1 = fma(T(P.c1), trQ, fma(T(P.hs1), vF6, fma(T(P.ns1), m1 - e1, m1)));
-    const T ms2 = fma(T(P.c2), trQ, fma(T(P.nhs2), vF6, fma(T(P.ns2), m2 - e2, m2)));
+    // m - m_eq for e and eps (Eq. 4): m1 + 2 rt - 3 rho|v|^2, m2 - rt + 3 rho|v|^2
+    const T n1 = fma(T(-3), ru2, fma(T(2), rt, m1));
+    const T n2 = fma(T(3), ru2, m2 - rt);
+    // S[1] = 6 v.F, S[2] = -6 v.F (Eq. 6): the 6 is folded into h6s1 = 6 hs1, nh6s2 = -6 hs2
+    const T ms1 = fma(T(P.c1), trQ, fma(T(P.h6s1), vF, fma(T(P.ns1), n1, m1)));
+    const T ms2 = fma(T(P.c2), trQ, fma(T(P.nh6s2), vF, fma(T(P.ns2), n2, m2)));
     const T ms3 = jx + Fx;                             // = m3 - s_j (m3 - rho v_x) + (1 - s_j/2) F_x
     const T ms4 = fma(T(P.nhs4), Fx, fma(T(P.ns4), m4 + rux, m4));
     const T ms5 = jy + Fy;
@@ -220,33 +221,33 @@ template <typename T> __device__ __forceinline__ T radicand_step(const EosRegs<T
 
 // Hybrid force (Eq. 9) and modifying tensor (Eq. 23, x G/2) of one node
 // from psi at the node (p0) and its eight neighbours (p_a at x + e_a).
-// negG = -G, hA = A/2, omA = 1 - A, kG2 = kappa G / 2.
+// The lattice sums are formed with the integer weights 12 w_a (4 on the
+// axes, 1 on the diagonals) and the common factor 1/12 is folded into the
+// constants: negGw = -G/12, kGw = kappa G/24; hA = A/2, omA = 1 - A.
 template <typename T>
-__device__ __forceinline__ void force_q(T negG, T hA, T omA, T kG2, T p0, T p1, T p2, T p3, T p4, T p5, T p6,
+__device__ __forceinline__ void force_q(T negGw, T hA, T omA, T kGw, T p0, T p1, T p2, T p3, T p4, T p5, T p6,
                                         T p7, T p8, T& Fx, T& Fy, T& Qxx, T& Qyy, T& Qxy) {
-    const T w1 = T(1.0 / 3.0), w2 = T(1.0 / 12.0);
     const T q1 = mul_rn(p1, p1), q2 = mul_rn(p2, p2), q3 = mul_rn(p3, p3), q4 = mul_rn(p4, p4);
     const T q5 = mul_rn(p5, p5), q6 = mul_rn(p6, p6), q7 = mul_rn(p7, p7), q8 = mul_rn(p8, p8);
     // Eq. 9: F = -G [ (A/2) sum w psi_n^2 e + (1-A) psi sum w psi_n e ]
-    const T gx1 = fma(w1, p1 - p3, w2 * ((p5 - p7) + (p8 - p6)));
-    const T gy1 = fma(w1, p2 - p4, w2 * ((p5 - p7) + (p6 - p8)));
-    const T gx2 = fma(w1, q1 - q3, w2 * ((q5 - q7) + (q8 - q6)));
-    const T gy2 = fma(w1, q2 - q4, w2 * ((q5 - q7) + (q6 - q8)));
+    const T a57 = p5 - p7, a86 = p8 - p6, b57 = q5 - q7, b86 = q8 - q6;
+    const T gx1 = fma(T(4), p1 - p3, a57 + a86), gy1 = fma(T(4), p2 - p4, a57 - a86);
+    const T gx2 = fma(T(4), q1 - q3, b57 + b86), gy2 = fma(T(4), q2 - q4, b57 - b86);
     const T c = omA * p0;
-    Fx = negG * fma(c, gx1, hA * gx2);
-    Fy = negG * fma(c, gy1, hA * gy2);
+    Fx = negGw * fma(c, gx1, hA * gx2);
+    Fy = negGw * fma(c, gy1, hA * gy2);
     // Eq. 23 (x G/2): sums of w (psi_n - psi) e e and w (psi_n^2 - psi^2) e e;
-    // sum w e_x^2 = sum w e_y^2 = 1 and sum w e_x e_y = 0 over the ring
-    const T d1 = w2 * ((p5 + p7) + (p6 + p8));
-    const T d2 = w2 * ((q5 + q7) + (q6 + q8));
+    // sum w e_x^2 = sum w e_y^2 = 1 (12 with the integer weights) and
+    // sum w e_x e_y = 0 over the ring
+    const T s57 = p5 + p7, s68 = p6 + p8, t57 = q5 + q7, t68 = q6 + q8;
+    const T d1 = s57 + s68, d2 = t57 + t68;
     const T q0 = mul_rn(p0, p0);
-    const T sxx1 = fma(w1, p1 + p3, d1) - p0, syy1 = fma(w1, p2 + p4, d1) - p0;
-    const T sxy1 = w2 * ((p5 + p7) - (p6 + p8));
-    const T sxx2 = fma(w1, q1 + q3, d2) - q0, syy2 = fma(w1, q2 + q4, d2) - q0;
-    const T sxy2 = w2 * ((q5 + q7) - (q6 + q8));
-    Qxx = kG2 * fma(c, sxx1, hA * sxx2);
-    Qyy = kG2 * fma(c, syy1, hA * syy2);
-    Qxy = kG2 * fma(c, sxy1, hA * sxy2);
+    const T sxx1 = fma(T(-12), p0, fma(T(4), p1 + p3, d1)), syy1 = fma(T(-12), p0, fma(T(4), p2 + p4, d1));
+    const T sxx2 = fma(T(-12), q0, fma(T(4), q1 + q3, d2)), syy2 = fma(T(-12), q0, fma(T(4), q2 + q4, d2));
+    const T sxy1 = s57 - s68, sxy2 = t57 - t68;
+    Qxx = kGw * fma(c, sxx1, hA * sxx2);
+    Qyy = kGw * fma(c, syy1, hA * syy2);
+    Qxy = kGw * fma(c, sxy1, hA * sxy2);
 }
 
 // One kernel, two ways to find the work: ONE = a single lattice whose
@@ -375,8 +376,8 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
         // neighbourhood slides down with it (three new loads per node)
         const Regs<T> R(P);
         const T G = P.G, A = P.A;
-        const T negG = -G, hA = T(0.5) * A, omA = T(1) - A;
-        const T kG2 = P.kappa * G * T(0.5);
+        const T negGw = -G * T(1.0 / 12.0), hA = T(0.5) * A, omA = T(1) - A;
+        const T kGw = P.kappa * G * T(1.0 / 24.0);
         const int ly0 = ty * Gm::ROWS;
         const T* s0 = sp + (ly0 + 1) * Gm::WP + (tx + 1);   // psi of node (tx, ly0)
         T wm0 = T(0), wm1 = T(0), wm2 = T(0), w00 = T(0), w01 = T(0), w02 = T(0);
@@ -408,7 +409,7 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
 
                 T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
                 if (interact)
-                    force_q<T>(negG, hA, omA, kG2, w01, w02, wp1, w00, wm1, wp2, wp0, wm0, wm2, Fx, Fy, Qxx, Qyy,
+                    force_q<T>(negGw, hA, omA, kGw, w01, w02, wp1, w00, wm1, wp2, wp0, wm0, wm2, Fx, Fy, Qxx, Qyy,
                                Qxy);
 
                 T out[9];
@@ -512,7 +513,8 @@ const Entry kF32[] = {
 };
 const Entry kF64[] = {
     LBM_CFG(double, 32, 8, 256, 1),  LBM_CFG(double, 64, 8, 256, 1), LBM_CFG(double, 32, 16, 256, 1),
-    LBM_CFG(double, 64, 4, 256, 1),  LBM_CFG(double, 32, 8, 256, 2),
+    LBM_CFG(double, 64, 4, 256, 1),  LBM_CFG(double, 32, 8, 256, 2),  LBM_CFG(double, 64, 16, 256, 1),
+    LBM_CFG(double, 32, 32, 256, 1),
 };
 
 const Entry* table(int prec, int* n) {

@@ -1,6 +1,6 @@
 """Parity at the benchmark's full size (4096x4096 spinodal), in the launch
-configuration bench.py times (tile 128x16, 512 threads, one tile per CTA,
-CUDA graphs), on sampled outputs the oracle can compute one by one.
+configuration bench.py times (its default tiles, one tile per CTA, CUDA
+graphs), on sampled outputs the oracle can compute one by one.
 
 A node's state after n steps depends only on the initial field within 2n
 nodes (the pull reaches one node, psi one more), so the oracle runs on a
@@ -16,6 +16,7 @@ import warnings
 import numpy as np
 import pytest
 
+import bench
 import lbm_inputs as I
 import oracle as O
 
@@ -73,7 +74,7 @@ def _oracle_window(op, rho0, cx, cy):
     return _oracle_on_window(op, rho0, idx_x, idx_y), idx_x, idx_y
 
 
-@pytest.mark.parametrize("prec,cfg,tol", [(1, 0, 1e-6), (2, 1, 1e-13)])
+@pytest.mark.parametrize("prec,cfg,tol", [(1, bench.TILE_FP32, 1e-6), (2, bench.TILE_FP64, 1e-13)])
 def test_bench_configuration_matches_oracle_on_sampled_windows(setup, prec, cfg, tol):
     P, eos, op, rho0 = setup
     lat = P.Lattice(N, N, prec)
@@ -96,7 +97,7 @@ def test_bench_configuration_matches_oracle_on_sampled_windows(setup, prec, cfg,
 def test_bench_configuration_conserves_mass(setup):
     P, eos, op, rho0 = setup
     lat = P.Lattice(N, N, P.LBM_FP32)
-    lat.set_schedule(0, 0)
+    lat.set_schedule(bench.TILE_FP32, 0)
     lat.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=0.25)
     lat.init_density(rho0)
     lat.use_graphs(True)
