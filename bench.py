@@ -105,16 +105,17 @@ def kernel_traffic(prec_name, kernel):
         return None
 
 
-def fp64_alu_roofline(mlups):
+def fp64_alu_roofline(mlups, kernel):
     """FP64 step against the FP64 pipe: GB300 issues 2 FP64 thread-operations
     per clock per SM; the kernel's FP64 operations per lattice update come
-    from the committed ncu summary (valid while the kernel is unchanged)."""
+    from the committed ncu summary (valid for the kernel it names, while the
+    kernel source is unchanged)."""
     src = os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", "lbm_step.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "step_fp64_1024_alu.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
-        if kv.get("lbm_step_cu_sha256_16") != sha:
+        if kv.get("lbm_step_cu_sha256_16") != sha or kv.get("kernel") != kernel:
             return None
         ops = float(kv["fp64_ops_per_update"])
     except (OSError, KeyError, ValueError):
@@ -331,7 +332,7 @@ def run_ours(args):
         fp64 = {"value": m64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1000.0,
                 "hbm_frac": 144 * N / (t64 / k64) / 1e9 / peak, "bytes_per_update": 144,
                 "kernel": "lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(P.lbm_tile_configs(P.LBM_FP64)[TILE_FP64])}
-        alu = fp64_alu_roofline(m64)
+        alu = fp64_alu_roofline(m64, fp64["kernel"])
         if alu:
             fp64["roofline"] = alu
         lat64.close()
