@@ -356,8 +356,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         lat.init_density(host_rho)
         lat.step(args.steps)
-        out = lat.read_fields(which=("rho",))["rho"]
-        out_rho[...] = out
+        lat.read_fields(which=("rho",), out={"rho": out_rho})
         t_e2e = time.perf_counter() - t0
         lat.close()
         e2e = {"value": N * args.steps / t_e2e / 1e6, "unit": "MLUPS",

@@ -322,9 +322,19 @@ class Batch:
     def clear_status(self):
         self._c(lib().lbm_clear_status(self.ctx))
 
-    def read_fields(self, i: int = 0, which=("rho", "ux", "uy", "psi")):
+    def read_fields(self, i: int = 0, which=("rho", "ux", "uy", "psi"), out=None):
+        """Macroscopic fields of instance i as (ny, nx) float64 arrays.  `out`
+        may supply the destination arrays (e.g. in pinned memory, which the
+        device-to-host copy then fills directly)."""
         shape = (self.ny[i], self.nx[i])
-        outs = {k: np.empty(shape) for k in which}
+        outs = {}
+        for k in which:
+            a = None if out is None else out.get(k)
+            if a is None:
+                a = np.empty(shape)
+            elif a.shape != shape or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+                raise ValueError("out[%r] must be a writeable C-contiguous float64 array of shape %s" % (k, shape))
+            outs[k] = a
         self._c(lib().lbm_batch_read_fields(self.ctx, i, *[_ptr(outs.get(k)) for k in ("rho", "ux", "uy", "psi")]))
         return outs
 

@@ -144,3 +144,24 @@ def test_lattice_with_more_than_2_31_population_elements(P):
         got = rho[np.ix_(iy, ix)][M:W - M, M:W - M]
         worst = max(worst, float(np.abs(got / ref - 1).max()))
     assert worst <= 1e-6, worst
+
+
+def test_read_fields_into_caller_arrays(P):
+    """read_fields fills caller-supplied (here pinned) arrays with the same
+    values it returns in fresh ones, and rejects a wrong shape or dtype."""
+    import torch
+    eos, op, rg, rl = _cs(P)
+    lat = P.Lattice(48, 40, P.LBM_FP32)
+    lat.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=rg)
+    lat.init_density(I.droplet_density(48, 40, 10, rl, rg))
+    lat.step(5)
+    ref = lat.read_fields()
+    pinned = {k: torch.empty((40, 48), dtype=torch.float64).pin_memory().numpy() for k in ("rho", "psi")}
+    got = lat.read_fields(which=("rho", "psi"), out=pinned)
+    assert got["rho"] is pinned["rho"] and got["psi"] is pinned["psi"]
+    assert np.array_equal(got["rho"], ref["rho"]) and np.array_equal(got["psi"], ref["psi"])
+    with pytest.raises(ValueError):
+        lat.read_fields(which=("rho",), out={"rho": np.empty((48, 40))})
+    with pytest.raises(ValueError):
+        lat.read_fields(which=("rho",), out={"rho": np.empty((40, 48), dtype=np.float32)})
+    lat.close()
