@@ -98,17 +98,21 @@ int lbm_laplace_fit(int n, const double* dp, const double* R, double* sigma, dou
 /* Bytes of device memory one context of these lattices needs when the caller
  * supplies dev_buf (populations of two time levels with their ghost layers,
  * per-instance descriptors, tile table, reduction and field scratch).
- * 0 on bad arguments (n < 1, any nx or ny < 2, unknown precision). */
+ * 0 on bad arguments (n < 1, any nx or ny outside [2, 2^20], unknown
+ * precision). */
 size_t lbm_required_bytes(int nx, int ny, int precision);
 size_t lbm_batch_required_bytes(int n, const int* nx, const int* ny, int precision);
 
 /* Create a context of one nx x ny periodic lattice (lbm_create) or of n
- * independent lattices (lbm_batch_create) in the given precision.
- * dev_buf: caller-owned device memory of at least the required bytes, 256-byte
- * aligned, or NULL to let the library allocate (and later free) its own.
- * stream: a cudaStream_t, or NULL for the legacy default stream.  Binds the
- * context to the calling thread's current device.  Parameters must be set
- * and a density initialised before the first lbm_step. */
+ * independent lattices (lbm_batch_create) in the given precision; nx and ny
+ * in [2, 2^20].  dev_buf: caller-owned device memory of at least the required
+ * bytes, 256-byte aligned, or NULL to let the library allocate (and later
+ * free) its own.  stream: a cudaStream_t, or NULL for the legacy default
+ * stream.  Binds the context to the calling thread's current device.
+ * Parameters must be set and a density initialised before the first
+ * lbm_step.  Errors (*out stays NULL): LBM_EINVAL for a bad shape, precision
+ * or a misaligned dev_buf; LBM_ENOMEM when buf_bytes is below the required
+ * size or the allocation fails; LBM_ECUDA when no device is usable. */
 int lbm_create(lbm_ctx** out, int nx, int ny, int precision, void* dev_buf, size_t buf_bytes,
                void* stream);
 int lbm_batch_create(lbm_ctx** out, int n, const int* nx, const int* ny, int precision,
@@ -121,7 +125,9 @@ void lbm_destroy(lbm_ctx* ctx);
  * surface-tension parameter kappa of Eq. 23, interaction strength G (only
  * its sign matters; G = 0 switches the interaction force and Q off),
  * relaxation rates s[9] (Eq. 2, moment order), the reference density rho_ref
- * subtracted from the FP32 populations, and LBM_FLAG_* flags. */
+ * subtracted from the FP32 populations, and LBM_FLAG_* flags.  LBM_EINVAL
+ * (parameters unchanged) for an unknown EOS, T <= 0, a non-finite A, kappa,
+ * G or rho_ref, or a rate outside (0, 2). */
 int lbm_set_params(lbm_ctx* ctx, const lbm_eos* eos, double A, double kappa, double G,
                    const double s[9], double rho_ref, unsigned flags);
 int lbm_batch_set_params(lbm_ctx* ctx, int i, const lbm_eos* eos, double A, double kappa,
