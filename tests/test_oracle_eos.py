@@ -109,3 +109,29 @@ def test_eq17_has_no_positive_pressure_coexistence_for_cs_at_0p7_with_small_A():
         rg, rl, _ = An.mechanical_stability(q)
         mg, ml, _ = An.maxwell(q)
         assert abs(rl / ml - 1) < 2e-3 and abs(rg / mg - 1) < 0.15
+
+
+def test_peng_robinson_critical_point_is_the_textbook_one():
+    """Peng-Robinson (Eq. 29) with a, b fixed and Tc = 0.07780 a / (0.45724 b R)
+    (the classic a = 0.45724 R^2 Tc^2 / pc, b = 0.07780 R Tc / pc): at T = Tc,
+    where alpha = 1, the isotherm has its inflection with zero slope at the
+    textbook critical volume v_c = 3.9514 b, with pc = 0.07780 R Tc / b and
+    Z_c = 0.3074 (to the 4-5 digits of those constants); just below Tc the
+    slope turns negative, just above it stays positive."""
+    a, b = 2 / 49, 2 / 21
+    Tc = 0.07780 * a / (0.45724 * b)
+    rc, pc = 1 / (3.9514 * b), 0.07780 * Tc / b
+
+    def params(T):
+        return O.Params(eos=O.EOS_PR, a=a, b=b, R=1.0, K=1.0, omega=0.344, Tc=Tc, T=T)
+
+    P = lambda q, r: O.pressure(q, np.asarray(r, dtype=np.float64))
+    p = params(Tc)
+    h = 1e-4 * rc
+    d1 = (P(p, rc + h) - P(p, rc - h)) / (2 * h)
+    d2 = (P(p, rc + h) - 2 * P(p, rc) + P(p, rc - h)) / h**2
+    assert abs(d1) / Tc < 1e-3 and abs(d2) * rc / Tc < 1e-3
+    assert abs(P(p, rc) / pc - 1) < 1e-3 and abs(P(p, rc) / (rc * Tc) - 0.3074) < 1e-3
+    rs = np.linspace(0.3 * rc, 2.0 * rc, 4001)
+    assert np.gradient(P(params(0.99 * Tc), rs), rs).min() < 0
+    assert np.gradient(P(params(1.01 * Tc), rs), rs).min() > 0
