@@ -245,7 +245,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1000.0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(args.nx, args.ny, "fp64", {"sample": "%dx%d" % (n, n)}),
+        "data": "synthetic",
+        # the workload of the arm it is compared with; the oracle computes it in FP64 on a sample
+        "config": workload_config(args.nx, args.ny, args.precision, {"sample": "%dx%d" % (n, n)}),
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
