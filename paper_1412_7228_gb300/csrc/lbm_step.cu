@@ -428,28 +428,29 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
     }
 }
 
-// The kernels.  FP32 single-lattice launches ask for 1024 resident threads
-// per SM (two CTAs of 512), which caps their registers at 64; the others
-// leave the register count to the compiler.
+// The kernels.  FP32 launches ask for 1024 resident threads per SM (two
+// CTAs of 512), which caps their registers at 64 (except the table-driven
+// persistent variant, which would spill); FP64 leaves the register count to
+// the compiler.
 template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
 __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, const int4* __restrict__ tiles,
                                              int ntiles, int parity, unsigned long long timeout_ns,
                                              const __grid_constant__ StepArgs<T> one) {
     step_body<T, BX, BY, NT, NBUF, ONE>(insts, tiles, ntiles, parity, timeout_ns, one);
 }
-template <int BX, int BY, int NT, int NBUF>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_step_f32(const Inst* __restrict__ insts,
+template <int BX, int BY, int NT, int NBUF, bool ONE>
+__global__ void __launch_bounds__(NT, (ONE || NBUF == 1) ? 1024 / NT : 1) k_step_f32(const Inst* __restrict__ insts,
                                                             const int4* __restrict__ tiles, int ntiles, int parity,
                                                             unsigned long long timeout_ns,
                                                             const __grid_constant__ StepArgs<float> one) {
-    step_body<float, BX, BY, NT, NBUF, true>(insts, tiles, ntiles, parity, timeout_ns, one);
+    step_body<float, BX, BY, NT, NBUF, ONE>(insts, tiles, ntiles, parity, timeout_ns, one);
 }
 // the kernel a (precision, ONE) launch uses
 template <typename T, int BX, int BY, int NT, int NBUF, bool ONE> struct KSel {
     static constexpr auto fn = &k_step<T, BX, BY, NT, NBUF, ONE>;
 };
-template <int BX, int BY, int NT, int NBUF> struct KSel<float, BX, BY, NT, NBUF, true> {
-    static constexpr auto fn = &k_step_f32<BX, BY, NT, NBUF>;
+template <int BX, int BY, int NT, int NBUF, bool ONE> struct KSel<float, BX, BY, NT, NBUF, ONE> {
+    static constexpr auto fn = &k_step_f32<BX, BY, NT, NBUF, ONE>;
 };
 
 // ---- tile configurations ------------------------------------------------
