@@ -308,7 +308,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     bpu = 72 if prec == P.LBM_FP32 else 144
     achieved = bpu * N / avg_launch / 1e9
-    kname = (("lbm::k_step_f32<%d,%d,%d,%d>" % tuple(tile)) if prec == P.LBM_FP32
+    kname = (("lbm::k_step_f32<%d,%d,%d,%d,1>" % tuple(tile)) if prec == P.LBM_FP32
              else ("lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(tile)))
     tpu = kernel_traffic(args.precision, kname)
     traffic = tpu * N if tpu is not None else None
