@@ -339,6 +339,37 @@ def run_ours(args):
             fp64["roofline"] = alu
         lat64.close()
 
+    # ---- the same step on the paper's other synthetic workloads -----------
+    # a static droplet (R = 0.2 L between the Maxwell densities) and a flat
+    # interface (liquid in the centre half), FP32 and FP64, same lattice size
+    others = None
+    if not args.no_workloads:
+        others = {}
+        eos_o = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
+        _, Tc_o, _ = P.lbm_eos_critical(eos_o)
+        eos_o.T = TR_CFG * Tc_o
+        rg, rl, _ = P.lbm_eos_maxwell(eos_o)
+        fields = {"droplet": I.droplet_density(nx, ny, 0.2 * min(nx, ny), rl, rg),
+                  "flat_interface": I.slab_density(nx, ny, rl, rg, width=4.0)}
+        for name, rho_init in fields.items():
+            res = {}
+            for pname, pr, kk, nsteps in (("fp32", P.LBM_FP32, TILE_FP32, 192), ("fp64", P.LBM_FP64, TILE_FP64, 32)):
+                lo = P.Lattice(nx, ny, pr)
+                lo.set_schedule(kk, 0)
+                lo.set_params(eos_o, A_CFG, KAPPA_CFG, G=-1.0, s=S_CFG, rho_ref=rg)
+                lo.init_density(rho_init)
+                lo.use_graphs(True)
+                lo.step(32)
+                lo.sync()
+                tt = time_steps(torch, lo, nsteps)
+                lo.sync()
+                lo.close()
+                m = N * nsteps / tt / 1e6
+                bb = 72 if pr == P.LBM_FP32 else 144
+                res[pname] = {"mlups": m, "hbm_frac": bb * N / (tt / nsteps) / 1e9 / peak, "steps": nsteps}
+            others[name] = res
+        del fields
+
     # ---- end to end through the public API with host buffers -------------
     e2e = None
     if not args.no_e2e:
@@ -382,7 +413,7 @@ def run_ours(args):
             "config": workload_config(nx, ny, args.precision, {"tile": list(tile), "graphs": True,
                                                        "parallelism": "replicas" if ws > 1 else "single"}),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": launches, "fp64": fp64, "status_ok": status_ok,
+            "gpu_launches": launches, "fp64": fp64, "other_workloads": others, "status_ok": status_ok,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -406,6 +437,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the droplet and flat-interface timings")
     ap.add_argument("--cpu-n", type=int, default=2048)
     ap.add_argument("--cpu-steps", type=int, default=8)
     args = ap.parse_args()
