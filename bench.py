@@ -202,6 +202,20 @@ def time_steps(torch, lat, steps):
     return e0.elapsed_time(e1) / 1000.0
 
 
+def cpu_model():
+    """The host CPU's model name (Linux), for the CPU-baseline record."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_mlups(nx, ny, steps):
     """The FP64 oracle as it stands, single-threaded, on a periodic nx x ny
     sample of the workload."""
@@ -248,7 +262,8 @@ def run_reference(args):
         "data": "synthetic",
         # the workload of the arm it is compared with; the oracle computes it in FP64 on a sample
         "config": workload_config(args.nx, args.ny, args.precision, {"sample": "%dx%d" % (n, n)}),
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count(), "cpu_model": cpu_model()},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -402,7 +417,8 @@ def run_ours(args):
         m, dt = cpu_oracle_mlups(cn, cn, args.cpu_steps)
         cpu = {"value": m, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                "sample": "%d steps of a %dx%d periodic sample of the workload (%.1f s), FP64 single-thread"
-                         % (args.cpu_steps, cn, cn, dt)}
+                         % (args.cpu_steps, cn, cn, dt),
+               "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
 
     if rank == 0:
         line = {
