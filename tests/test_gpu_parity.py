@@ -1,6 +1,6 @@
 """GPU-vs-oracle parity of the fused sm_103a step, through the C ABI.
 
-Tolerances (derivation in DESIGN.md, "Parity tolerances"):
+Tolerances, from the arithmetic of the two paths:
   FP64: the kernel evaluates the same formulas in a different order (unrolled
         moments, fused multiply-adds); after n steps of a dissipative update
         the populations agree to ~1e-15 n relative -> 1e-12 for n <= 100.
