@@ -158,8 +158,11 @@ def laplace_sweep(radii=(20, 30, 40, 50, 60), kappas=(0.0, 0.1, 0.3, 0.5), t_ove
 
 
 def sweep_droplets(n=64, seed=7228, sizes=(128, 256, 512, 1024), A_shift=-0.7) -> List[Droplet]:
-    """The batched uneven sweep's instances; A is drawn from the configured
-    range shifted by A_shift (see the design notes on the hybrid weight A)."""
+    """The batched uneven sweep's instances.  A is drawn from U[-0.2, -0.1]
+    shifted by A_shift: with the forcing of Eqs. 5-6, eps = -2A of Eq. 17 so
+    small leaves the Carnahan-Starling law without a coexistence state of
+    positive pressure below about 0.75 Tc, while A near -0.85 keeps it within
+    0.2 % (liquid) of Maxwell's densities at 0.6-0.8 Tc."""
     return [Droplet(s.L, s.radius, s.T_over_Tc, s.A + A_shift, s.kappa)
             for s in I.sweep_instances(n, seed, sizes)]
 
