@@ -224,11 +224,12 @@ template <typename T> __device__ __forceinline__ T radicand_step(const EosRegs<T
 // The lattice sums are formed with the integer weights 12 w_a (4 on the
 // axes, 1 on the diagonals) and the common factor 1/12 is folded into the
 // constants: negGw = -G/12, kGw = kappa G/24; hA = A/2, omA = 1 - A.
+// q_a = p_a^2, rounded on their own (the caller slides them down a column
+// with the psi values, so each square is formed once).
 template <typename T>
 __device__ __forceinline__ void force_q(T negGw, T hA, T omA, T kGw, T p0, T p1, T p2, T p3, T p4, T p5, T p6,
-                                        T p7, T p8, T& Fx, T& Fy, T& Qxx, T& Qyy, T& Qxy) {
-    const T q1 = mul_rn(p1, p1), q2 = mul_rn(p2, p2), q3 = mul_rn(p3, p3), q4 = mul_rn(p4, p4);
-    const T q5 = mul_rn(p5, p5), q6 = mul_rn(p6, p6), q7 = mul_rn(p7, p7), q8 = mul_rn(p8, p8);
+                                        T p7, T p8, T q0, T q1, T q2, T q3, T q4, T q5, T q6, T q7, T q8, T& Fx,
+                                        T& Fy, T& Qxx, T& Qyy, T& Qxy) {
     // Eq. 9: F = -G [ (A/2) sum w psi_n^2 e + (1-A) psi sum w psi_n e ]
     const T a57 = p5 - p7, a86 = p8 - p6, b57 = q5 - q7, b86 = q8 - q6;
     const T gx1 = fma(T(4), p1 - p3, a57 + a86), gy1 = fma(T(4), p2 - p4, a57 - a86);
@@ -241,7 +242,6 @@ __device__ __forceinline__ void force_q(T negGw, T hA, T omA, T kGw, T p0, T p1,
     // sum w e_x e_y = 0 over the ring
     const T s57 = p5 + p7, s68 = p6 + p8, t57 = q5 + q7, t68 = q6 + q8;
     const T d1 = s57 + s68, d2 = t57 + t68;
-    const T q0 = mul_rn(p0, p0);
     const T sxx1 = fma(T(-12), p0, fma(T(4), p1 + p3, d1)), syy1 = fma(T(-12), p0, fma(T(4), p2 + p4, d1));
     const T sxx2 = fma(T(-12), q0, fma(T(4), q1 + q3, d2)), syy2 = fma(T(-12), q0, fma(T(4), q2 + q4, d2));
     const T sxy1 = s57 - s68, sxy2 = t57 - t68;
@@ -380,7 +380,12 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
         const T kGw = P.kappa * G * T(1.0 / 24.0);
         const int ly0 = ty * Gm::ROWS;
         const T* s0 = sp + (ly0 + 1) * Gm::WP + (tx + 1);   // psi of node (tx, ly0)
+        // FP64 slides the squares of the window too (six FP64 products fewer
+        // per node); FP32 forms them per node, which keeps it to fewer
+        // registers and measured faster
+        constexpr bool kSlideSquares = sizeof(T) == 8;
         T wm0 = T(0), wm1 = T(0), wm2 = T(0), w00 = T(0), w01 = T(0), w02 = T(0);
+        T qm0 = T(0), qm1 = T(0), qm2 = T(0), q00 = T(0), q01 = T(0), q02 = T(0);   // their squares
         if (interact) {
             wm0 = s0[-Gm::WP - 1];
             wm1 = s0[-Gm::WP];
@@ -388,18 +393,31 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
             w00 = s0[-1];
             w01 = s0[0];
             w02 = s0[1];
+            if (kSlideSquares) {
+                qm0 = mul_rn(wm0, wm0);
+                qm1 = mul_rn(wm1, wm1);
+                qm2 = mul_rn(wm2, wm2);
+                q00 = mul_rn(w00, w00);
+                q01 = mul_rn(w01, w01);
+                q02 = mul_rn(w02, w02);
+            }
         }
 
 #pragma unroll
         for (int r = 0; r < Gm::ROWS; ++r) {
             const int ly = ly0 + r;
             const int x = x0 + tx, y = y0 + ly;
-            T wp0 = T(0), wp1 = T(0), wp2 = T(0);
+            T wp0 = T(0), wp1 = T(0), wp2 = T(0), qp0 = T(0), qp1 = T(0), qp2 = T(0);
             if (interact) {
                 const T* sr = s0 + (r + 1) * Gm::WP;
                 wp0 = sr[-1];
                 wp1 = sr[0];
                 wp2 = sr[1];
+                if (kSlideSquares) {
+                    qp0 = mul_rn(wp0, wp0);
+                    qp1 = mul_rn(wp1, wp1);
+                    qp2 = mul_rn(wp2, wp2);
+                }
             }
             if (x < nx && y < ny) {
                 const T* q = sf + (ly + GY) * Gm::WB + (tx + Gm::HX);
@@ -408,9 +426,21 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
                 for (int a = 0; a < 9; ++a) f[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
 
                 T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
-                if (interact)
-                    force_q<T>(negGw, hA, omA, kGw, w01, w02, wp1, w00, wm1, wp2, wp0, wm0, wm2, Fx, Fy, Qxx, Qyy,
-                               Qxy);
+                if (interact) {
+                    if (!kSlideSquares) {
+                        qp0 = mul_rn(wp0, wp0);
+                        qp1 = mul_rn(wp1, wp1);
+                        qp2 = mul_rn(wp2, wp2);
+                        qm0 = mul_rn(wm0, wm0);
+                        qm1 = mul_rn(wm1, wm1);
+                        qm2 = mul_rn(wm2, wm2);
+                        q00 = mul_rn(w00, w00);
+                        q01 = mul_rn(w01, w01);
+                        q02 = mul_rn(w02, w02);
+                    }
+                    force_q<T>(negGw, hA, omA, kGw, w01, w02, wp1, w00, wm1, wp2, wp0, wm0, wm2, q01, q02, qp1, q00,
+                               qm1, qp2, qp0, qm0, qm2, Fx, Fy, Qxx, Qyy, Qxy);
+                }
 
                 T out[9];
                 collide<T>(R, f, Fx, Fy, Qxx, Qyy, Qxy, out);
@@ -423,6 +453,8 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
             }
             wm0 = w00; wm1 = w01; wm2 = w02;
             w00 = wp0; w01 = wp1; w02 = wp2;
+            qm0 = q00; qm1 = q01; qm2 = q02;
+            q00 = qp0; q01 = qp1; q02 = qp2;
         }
         if (bad) atomicOr(status, ST_UNSTABLE);
     }
