@@ -208,8 +208,12 @@ def cpu_model():
         with open("/proc/cpuinfo") as fh:
             for line in fh:
                 key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu part", "hardware"):
+                if key == "model name":
                     return line.split(":", 1)[1].strip()
+                if key == "cpu part":   # Arm: the part number (0xd4f = Neoverse V2, as in Grace)
+                    part = line.split(":", 1)[1].strip()
+                    names = {"0xd4f": "Neoverse V2", "0xd40": "Neoverse V1", "0xd0c": "Neoverse N1"}
+                    return "Arm %s (part %s)" % (names.get(part, "core"), part)
     except OSError:
         pass
     import platform
