@@ -202,10 +202,10 @@ def time_steps(torch, lat, steps):
     return e0.elapsed_time(e1) / 1000.0
 
 
-def cpu_model():
+def cpu_model(cpuinfo="/proc/cpuinfo"):
     """The host CPU's model name (Linux), for the CPU-baseline record."""
     try:
-        with open("/proc/cpuinfo") as fh:
+        with open(cpuinfo) as fh:
             for line in fh:
                 key = line.split(":")[0].strip().lower()
                 if key == "model name":

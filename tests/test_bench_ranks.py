@@ -77,3 +77,22 @@ def test_traffic_figure_is_used_only_for_the_profiled_kernel():
     else:
         assert got is None
     assert bench.kernel_traffic("fp32", "lbm::some_other_kernel") is None
+
+
+def test_fp64_roofline_and_cpu_model_records(tmp_path):
+    """The FP64 ALU roofline uses the committed operation count only for the
+    kernel it names; the CPU model is read from x86 and Arm cpuinfo alike."""
+    sys.path.insert(0, ROOT)
+    import bench
+    path = os.path.join(ROOT, "profiles", "step_fp64_1024_alu.txt")
+    kv = dict(l.strip().split("=", 1) for l in open(path) if "=" in l and not l.startswith("#"))
+    r = bench.fp64_alu_roofline(2000.0, kv["kernel"])
+    if r is not None:
+        assert r["bound"] == "alu" and abs(r["frac"] - 2000.0e6 * float(kv["fp64_ops_per_update"]) / 1e9 / r["peak"]) < 1e-12
+    assert bench.fp64_alu_roofline(2000.0, "lbm::another_kernel") is None
+    x86 = tmp_path / "x86"
+    x86.write_text("processor\t: 0\nmodel name\t: Some CPU @ 2.0GHz\n")
+    arm = tmp_path / "arm"
+    arm.write_text("processor\t: 0\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
+    assert bench.cpu_model(str(x86)) == "Some CPU @ 2.0GHz"
+    assert bench.cpu_model(str(arm)) == "Arm Neoverse V2 (part 0xd4f)"
