@@ -206,7 +206,8 @@ int lbm_load(lbm_ctx* ctx, const char* path);
 int lbm_tile_config_count(int precision);
 int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads, int* stages);
 /* Select tile configuration k and CTA schedule (0: instance-major row
- * order, 1: tiles of all instances interleaved, 2: largest instance first). */
+ * order, 1: the tiles of each launch's instances interleaved, 2: largest
+ * instance first).  A batch is stepped by one launch per 64 instances. */
 int lbm_set_schedule(lbm_ctx* ctx, int tile_config, int schedule);
 /* Time every (tile configuration, schedule) pair over `steps` steps of the
  * current state (which is restored afterwards) and keep the fastest.

@@ -19,6 +19,12 @@ namespace {
 constexpr unsigned long long kTimeoutNs = 1000000000ull;   // bounded TMA wait: 1 s
 constexpr int kGraphSteps = 32;                            // steps per captured graph (even)
 
+// The TMA tensor maps of one instance's two time levels (host copies; the
+// kernels receive them in their argument blocks).
+struct Maps {
+    CUtensorMap tmap[2];
+};
+
 struct HostParams {
     lbm_eos eos;
     double A, kappa, G, s[9], rho_ref;
@@ -203,7 +209,12 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     Inst* d_inst = nullptr;
     int4* d_tiles = nullptr;
-    int ntiles = 0;
+    int ntiles = 0;                   // tiles of all instances
+    std::vector<Maps> maps;
+    // a batch (n > 1) is stepped by one launch per chunk of up to
+    // kBatchLaunchMax instances: argument blocks per time-level parity
+    std::vector<lbm::BatchArgs> bargs[2];
+    std::vector<int> chunk_tiles;
     int* d_status = nullptr;
     double* d_partials = nullptr;
     double* d_result = nullptr;
@@ -258,7 +269,7 @@ int encode_maps(lbm_ctx* c) {
                                      static_cast<cuuint64_t>(I.plane) * c->esz};
             cuuint32_t box[3] = {static_cast<cuuint32_t>(t.bx + 2 * HX), static_cast<cuuint32_t>(t.by + 2 * lbm::GY), 9};
             cuuint32_t es[3] = {1, 1, 1};
-            CUresult r = enc(&I.tmap[k], c->prec == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+            CUresult r = enc(&c->maps[i].tmap[k], c->prec == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                              3, I.pop[k], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -282,8 +293,8 @@ int upload_insts(lbm_ctx* c) {
 // block); refreshed whenever the tensor maps or the parameters change.
 template <typename T> void fill_one(lbm_ctx* c, lbm::StepArgs<T>& a, const lbm::Phys<T>& P) {
     const Inst& I = c->h[0];
-    a.tmap[0] = I.tmap[0];
-    a.tmap[1] = I.tmap[1];
+    a.tmap[0] = c->maps[0].tmap[0];
+    a.tmap[1] = c->maps[0].tmap[1];
     a.P = P;
     a.pop[0] = I.pop[0];
     a.pop[1] = I.pop[1];
@@ -306,33 +317,84 @@ const void* one_args(lbm_ctx* c) {
     return c->prec == LBM_FP32 ? static_cast<const void*>(&c->one_f) : static_cast<const void*>(&c->one_d);
 }
 
+// Tiles and argument blocks for the current tile configuration and schedule.
+// Instances are ordered (schedule 0: by index, 1: by index with the tiles of
+// each chunk's instances interleaved through a tile table, 2: most tiles
+// first) and cut into chunks of kBatchLaunchMax; a chunk's tiles run in slot
+// order, row-major within an instance, unless it has a tile table.
 int build_tiles(lbm_ctx* c) {
     const lbm::TileCfg t = lbm::step_config(c->prec, c->cfg);
-    std::vector<std::vector<int4>> per(c->n);
+    std::vector<int> tx(c->n), cnt(c->n);
+    size_t total = 0;
     for (int i = 0; i < c->n; ++i) {
-        const int tx = (c->nx[i] + t.bx - 1) / t.bx, ty = (c->ny[i] + t.by - 1) / t.by;
-        for (int y = 0; y < ty; ++y)
-            for (int x = 0; x < tx; ++x) per[i].push_back(make_int4(i, x * t.bx, y * t.by, 0));
+        tx[i] = (c->nx[i] + t.bx - 1) / t.bx;
+        cnt[i] = tx[i] * ((c->ny[i] + t.by - 1) / t.by);
+        total += static_cast<size_t>(cnt[i]);
     }
+    if (total > c->L.tiles_cap || total > 0x7fffffff) return fail(c, LBM_ENOMEM, "tile table larger than reserved%s");
+    c->ntiles = static_cast<int>(total);
+    for (auto& v : c->bargs) v.clear();
+    c->chunk_tiles.clear();
+    if (c->n == 1) return LBM_OK;   // one lattice: StepArgs, tiles from blockIdx
+
     std::vector<int> order(c->n);
     for (int i = 0; i < c->n; ++i) order[i] = i;
-    std::vector<int4> all;
-    if (c->sched == 1) {
-        size_t most = 0;
-        for (auto& v : per) most = std::max(most, v.size());
-        for (size_t k = 0; k < most; ++k)
-            for (int i = 0; i < c->n; ++i)
-                if (k < per[i].size()) all.push_back(per[i][k]);
-    } else {
-        if (c->sched == 2)
-            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
-        for (int i : order) all.insert(all.end(), per[i].begin(), per[i].end());
+    if (c->sched == 2) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
+    std::vector<int4> table;   // schedule 1: every chunk's table, one after another
+    for (int c0 = 0; c0 < c->n; c0 += lbm::kBatchLaunchMax) {
+        const int m = std::min(lbm::kBatchLaunchMax, c->n - c0);
+        lbm::BatchArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.n = m;
+        int first = 0;
+        for (int k = 0; k < m; ++k) {
+            const int i = order[c0 + k];
+            a.inst[k] = i;
+            a.tiles_x[k] = tx[i];
+            lbm::tile_row_magic(tx[i], &a.div_m[k], &a.div_s[k]);
+            for (int r = 0; r < cnt[i]; ++r)   // the kernel's row of every tile of the instance
+                if (lbm::tile_row(r, a.div_m[k], a.div_s[k]) != r / tx[i])
+                    return fail(c, LBM_EINVAL, "tile row by multiplication disagrees with division%s");
+            a.first[k] = first;
+            first += cnt[i];
+        }
+        a.first[m] = first;
+        if (c->sched == 1) {
+            a.tiles = c->d_tiles + table.size();
+            int most = 0;
+            for (int k = 0; k < m; ++k) most = std::max(most, cnt[a.inst[k]]);
+            for (int r = 0; r < most; ++r)
+                for (int k = 0; k < m; ++k)
+                    if (r < cnt[a.inst[k]])
+                        table.push_back(make_int4(k, (r % a.tiles_x[k]) * t.bx, (r / a.tiles_x[k]) * t.by, 0));
+        }
+        for (int par = 0; par < 2; ++par) {
+            for (int k = 0; k < m; ++k) a.tmap[k] = c->maps[a.inst[k]].tmap[par];
+            c->bargs[par].push_back(a);
+        }
+        c->chunk_tiles.push_back(first);
     }
-    if (all.size() > c->L.tiles_cap) return fail(c, LBM_ENOMEM, "tile table larger than reserved%s");
-    c->ntiles = static_cast<int>(all.size());
-    CK(c, cudaMemcpyAsync(c->d_tiles, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
+    if (!table.empty()) {
+        CK(c, cudaMemcpyAsync(c->d_tiles, table.data(), table.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                              c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
     return LBM_OK;
+}
+
+// Kernel launches of one step, and their issue on a stream.
+int step_launches(const lbm_ctx* c) { return c->n == 1 ? 1 : static_cast<int>(c->chunk_tiles.size()); }
+
+cudaError_t launch_step(lbm_ctx* c, int parity) {
+    if (c->n == 1)
+        return lbm::step_launch(c->prec, c->cfg, c->d_inst, one_args(c), true, c->ntiles, parity, kTimeoutNs,
+                                c->stream);
+    for (size_t j = 0; j < c->chunk_tiles.size(); ++j) {
+        cudaError_t e = lbm::step_launch(c->prec, c->cfg, c->d_inst, &c->bargs[parity][j], false, c->chunk_tiles[j],
+                                         parity, kTimeoutNs, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 int apply_schedule(lbm_ctx* c, int cfg, int sched) {
@@ -423,10 +485,9 @@ int sync_all(lbm_ctx* c) {
 
 int launch_steps(lbm_ctx* c, int n) {
     for (int k = 0; k < n; ++k) {
-        CK(c, lbm::step_launch(c->prec, c->cfg, c->d_inst, c->d_tiles, c->ntiles, c->parity, kTimeoutNs, one_args(c),
-                               c->stream));
+        CK(c, launch_step(c, c->parity));
         c->parity ^= 1;
-        ++c->launches;
+        c->launches += step_launches(c);
         ++c->steps;
     }
     return LBM_OK;
@@ -437,8 +498,7 @@ int ensure_graph(lbm_ctx* c, int parity) {
     cudaGraph_t g;
     CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < kGraphSteps; ++k) {
-        cudaError_t e = lbm::step_launch(c->prec, c->cfg, c->d_inst, c->d_tiles, c->ntiles, parity ^ (k & 1),
-                                         kTimeoutNs, one_args(c), c->stream);
+        cudaError_t e = launch_step(c, parity ^ (k & 1));
         if (e != cudaSuccess) {
             cudaStreamEndCapture(c->stream, &g);
             return cuda_fail(c, e, "step launch during graph capture");
@@ -616,6 +676,7 @@ int lbm_batch_create(lbm_ctx** out, int n, const int* nx, const int* ny, int pre
     c->d_result = reinterpret_cast<double*>(c->buf + c->L.result_off);
     c->d_scratch = reinterpret_cast<double*>(c->buf + c->L.scratch_off);
     c->h.assign(n, Inst{});
+    c->maps.assign(n, Maps{});
     for (int i = 0; i < n; ++i) {
         Inst& I = c->h[i];
         std::memset(&I, 0, sizeof(Inst));
@@ -754,7 +815,7 @@ int lbm_step(lbm_ctx* c, int n) {
             rc = ensure_graph(c, c->parity);
             if (rc) return rc;
             CK(c, cudaGraphLaunch(c->gexec[c->parity], c->stream));
-            c->launches += kGraphSteps;
+            c->launches += static_cast<long long>(kGraphSteps) * step_launches(c);
             c->steps += kGraphSteps;
             n -= kGraphSteps;   // an even number of steps: parity is unchanged
         }

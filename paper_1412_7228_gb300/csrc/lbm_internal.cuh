@@ -60,10 +60,9 @@ template <typename T> struct Phys {
     T nu_g, dnu, visc_rho_g, visc_inv_drho;
 };
 
-// One lattice.  The two tensor maps come first: a CUtensorMap must sit on a
-// 64-byte boundary in global memory.
+// One lattice, as the kernels see it in global memory.  Its TMA tensor maps
+// are not here: they travel in the kernel argument blocks below.
 struct alignas(128) Inst {
-    CUtensorMap tmap[2];     // 3-D maps {pitch, nyp, 9} of pop[0], pop[1]
     void* pop[2];
     int* status;
     int nx, ny, pitch, nyp;  // pitch, nyp in elements
@@ -85,6 +84,44 @@ template <typename T> struct StepArgs {   // CUtensorMap members give it their a
     long long plane;
     int nx, ny, pitch, tiles_x;
 };
+
+// What a batched launch needs to find its tiles, passed by value as a
+// __grid_constant__ kernel argument as well: the tensor maps of up to
+// kBatchLaunchMax instances (in parameter space a map needs neither a
+// load of its own nor a tensormap proxy fence, which a map in global memory
+// needs before every first use in a CTA) and their tile counts.  Slot k's
+// tiles are first[k] .. first[k+1]-1, row-major over tiles_x[k] columns;
+// with a tile table (the interleaved schedule) entry t gives (slot, x0, y0)
+// instead.  A batch with more instances is stepped by several launches.
+constexpr int kBatchLaunchMax = 64;
+struct BatchArgs {
+    CUtensorMap tmap[kBatchLaunchMax];   // maps of the source time level of slot k
+    const int4* tiles;                   // tile table, or nullptr: tiles in slot order
+    int first[kBatchLaunchMax + 1];      // first tile of slot k; first[n] = tiles of the launch
+    int tiles_x[kBatchLaunchMax];        // tile columns of slot k
+    unsigned div_m[kBatchLaunchMax];     // division by tiles_x[k]: see tile_row()
+    int div_s[kBatchLaunchMax];
+    int inst[kBatchLaunchMax];           // slot k -> index into the Inst array
+    int n;                               // slots in use, 1..kBatchLaunchMax
+};
+
+// floor(r / d) for 0 <= r < 2^31 and d >= 1 as one 64-bit multiply and a
+// shift (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d), m = ceil(2^(31+l) / d) and
+// s = 31 + l, m d - 2^s lies in [0, d - 1] and d <= 2^l, so
+// r m / 2^s = r / d + e with 0 <= e < 1/d, which cannot reach the next
+// integer; m < 2^32.  The host computes (m, s) per instance and checks the
+// result for every tile it launches.
+__host__ __device__ __forceinline__ int tile_row(int r, unsigned m, int s) {
+    return static_cast<int>((static_cast<unsigned long long>(r) * m) >> s);
+}
+inline void tile_row_magic(int d, unsigned* m, int* s) {
+    int l = 0;
+    while ((1ll << l) < d) ++l;
+    *s = 31 + l;
+    *m = static_cast<unsigned>(((1ull << (31 + l)) + static_cast<unsigned long long>(d) - 1) /
+                               static_cast<unsigned long long>(d));
+}
 
 template <typename T> __device__ __forceinline__ const Phys<T>& phys(const Inst* I);
 template <> __device__ __forceinline__ const Phys<float>& phys<float>(const Inst* I) { return I->pf; }
@@ -169,14 +206,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// The tensor maps sit in global memory and the host rewrites them when the
-// tile shape changes: acquire them through the tensormap proxy before use.
-__device__ __forceinline__ void acquire_tmap(const CUtensorMap* map) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
-                 : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-
 }  // namespace lbm
 
 // ---- host-side interfaces between the translation units -----------------
@@ -189,10 +218,11 @@ int step_config_count(int prec);
 TileCfg step_config(int prec, int k);
 size_t step_smem_bytes(int prec, int k);
 cudaError_t step_prepare(int prec, int k);   // sets the dynamic smem attribute
-// one: a StepArgs<float> / StepArgs<double> for a context of one lattice
-// (tile coordinates from blockIdx), or nullptr to use the tile table.
-cudaError_t step_launch(int prec, int k, const Inst* d_insts, const int4* d_tiles, int ntiles,
-                        int parity, unsigned long long timeout_ns, const void* one, cudaStream_t st);
+// args: a StepArgs<float> / StepArgs<double> for a context of one lattice
+// (one = true; tile coordinates from blockIdx), else a BatchArgs of up to
+// kBatchLaunchMax instances.  ntiles: tiles this launch steps.
+cudaError_t step_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int parity,
+                        unsigned long long timeout_ns, cudaStream_t st);
 
 // Auxiliary kernels (lbm_aux.cu); `host` is the host copy of the descriptor.
 cudaError_t aux_init(const Inst& host, const Inst* d_inst, const double* rho, const double* ux,

@@ -18,6 +18,8 @@
 // Each population is read from and written to HBM once per step; the halo
 // re-reads of neighbouring tiles are served from L2.  No tensor cores: the
 // 9x9 transforms have integer entries and are unrolled into adds.
+#include <type_traits>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -250,15 +252,28 @@ __device__ __forceinline__ void force_q(T negGw, T hA, T omA, T kGw, T p0, T p1,
     Qxy = kGw * fma(c, sxy1, hA * sxy2);
 }
 
-// One kernel, two ways to find the work: ONE = a single lattice whose
-// constants and tensor maps arrive in the __grid_constant__ argument, tile
-// coordinates from the tile index; otherwise a tile table over instances
-// whose descriptors live in global memory.  NBUF = 2 makes the CTAs
-// persistent with a two-stage TMA pipeline: while tile k is collided, the
-// box of tile k+1 streams into the other shared-memory buffer.
-template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
-__device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const int4* __restrict__ tiles, int ntiles,
-                                          int parity, unsigned long long timeout_ns, const StepArgs<T>& one) {
+// The constants of the lattice a tile belongs to: in the one-lattice
+// argument block (parameter space), or in an instance descriptor in global
+// memory.
+template <typename T> __device__ __forceinline__ const Phys<T>& phys_of(const StepArgs<T>& a, const Inst*) {
+    return a.P;
+}
+template <typename T> __device__ __forceinline__ const Phys<T>& phys_of(const BatchArgs&, const Inst* I) {
+    return phys<T>(I);
+}
+
+// One kernel, two ways to find the work, both from a __grid_constant__
+// argument block: ONE = a single lattice (StepArgs: constants and tensor
+// maps; tile coordinates from the tile index); otherwise a BatchArgs over up
+// to kBatchLaunchMax instances (tensor maps and tile counts; the tile's
+// instance by a binary search of the tile counts' prefix sums, or from a tile
+// table; constants from the instance's descriptor in global memory).
+// NBUF = 2 makes the CTAs persistent with a two-stage TMA pipeline: while
+// tile k is collided, the box of tile k+1 streams into the other
+// shared-memory buffer.
+template <typename T, int BX, int BY, int NT, int NBUF, bool ONE, typename Args>
+__device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int ntiles, int parity,
+                                          unsigned long long timeout_ns, const Args& a) {
     using Gm = Geom<T, BX, BY, NT, NBUF>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -274,27 +289,39 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
     }
     __syncthreads();
 
-    auto tile_of = [&](int tt, int& inst, int& x0, int& y0) {
-        if (ONE) {
-            inst = 0;
-            x0 = (tt % one.tiles_x) * BX;
-            y0 = (tt / one.tiles_x) * BY;
+    // tile tt -> (slot, x0, y0); the slot indexes the argument block's instances
+    auto tile_of = [&](int tt, int& slot, int& x0, int& y0) {
+        if constexpr (ONE) {
+            slot = 0;
+            x0 = (tt % a.tiles_x) * BX;
+            y0 = (tt / a.tiles_x) * BY;
         } else {
-            const int4 tl = tiles[tt];
-            inst = tl.x;
-            x0 = tl.y;
-            y0 = tl.z;
+            if (a.tiles) {
+                const int4 tl = a.tiles[tt];
+                slot = tl.x;
+                x0 = tl.y;
+                y0 = tl.z;
+            } else {
+                int lo = 0, hi = a.n - 1;   // the last slot with first[slot] <= tt
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.first[mid] <= tt) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int r = tt - a.first[lo];
+                const int q = tile_row(r, a.div_m[lo], a.div_s[lo]);   // r / tiles_x
+                slot = lo;
+                x0 = (r - q * a.tiles_x[lo]) * BX;
+                y0 = q * BY;
+            }
         }
     };
-    int last_inst = -1;   // thread 0 only: instance whose tensor map was last acquired
     auto issue = [&](int tt, int bb) {
-        int inst, x0, y0;
-        tile_of(tt, inst, x0, y0);
-        const CUtensorMap* map = ONE ? &one.tmap[parity] : &insts[inst].tmap[parity];
-        if (!ONE && inst != last_inst) {
-            acquire_tmap(map);
-            last_inst = inst;
-        }
+        int slot, x0, y0;
+        tile_of(tt, slot, x0, y0);
+        const CUtensorMap* map;
+        if constexpr (ONE) map = &a.tmap[parity];
+        else map = &a.tmap[slot];
         mbar_arrive_expect_tx(&bar[bb], static_cast<uint32_t>(Gm::box_bytes));
         tma_load_3d(smem + bb * Gm::buf_stride, map, x0 + Gm::GX - Gm::HX, y0, 0, &bar[bb]);
     };
@@ -306,12 +333,22 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
         const uint32_t ph = NBUF == 2 ? ((k >> 1) & 1) : (k & 1);
         const T* sf = reinterpret_cast<const T*>(smem + b * Gm::buf_stride);
         T* sp = reinterpret_cast<T*>(smem + Gm::psi_off + b * Gm::psi_stride);
-        int inst, x0, y0;
-        tile_of(t, inst, x0, y0);
-        const Inst* I = ONE ? nullptr : insts + inst;
-        const Phys<T>& P = ONE ? one.P : phys<T>(I);
-        const int nx = ONE ? one.nx : I->nx, ny = ONE ? one.ny : I->ny;
-        int* status = ONE ? one.status : I->status;
+        int slot, x0, y0;
+        tile_of(t, slot, x0, y0);
+        const Inst* I = nullptr;
+        if constexpr (!ONE) I = insts + a.inst[slot];
+        const Phys<T>& P = phys_of<T>(a, I);
+        int nx, ny;
+        int* status;
+        if constexpr (ONE) {
+            nx = a.nx;
+            ny = a.ny;
+            status = a.status;
+        } else {
+            nx = I->nx;
+            ny = I->ny;
+            status = I->status;
+        }
         const int interact = P.interact;
         const EosRegs<T> E(P);
         const T rho_ref = P.rho_ref;
@@ -351,9 +388,18 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
         if (NBUF == 2 && tid == 0 && t + static_cast<int>(gridDim.x) < ntiles) issue(t + gridDim.x, b ^ 1);
 
         // ---- collide and stream every owned node -------------------------
-        T* __restrict__ dst = static_cast<T*>(ONE ? one.pop[parity ^ 1] : I->pop[parity ^ 1]);
-        const long long plane = ONE ? one.plane : I->plane;
-        const int pitch = ONE ? one.pitch : I->pitch;
+        T* __restrict__ dst;
+        long long plane;
+        int pitch;
+        if constexpr (ONE) {
+            dst = static_cast<T*>(a.pop[parity ^ 1]);
+            plane = a.plane;
+            pitch = a.pitch;
+        } else {
+            dst = static_cast<T*>(I->pop[parity ^ 1]);
+            plane = I->plane;
+            pitch = I->pitch;
+        }
         const bool border = x0 < 2 || x0 + BX > nx - 2 || y0 < 2 || y0 + BY > ny - 2;
         // periodic images in the ghost cells read by the neighbouring tiles
         auto ghost = [&](T* o, int x, int y, const T (&v)[9]) {
@@ -461,27 +507,42 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, const 
 }
 
 // The kernels.  FP32 launches ask for 1024 resident threads per SM (two
-// CTAs of 512), which caps their registers at 64 (except the table-driven
+// CTAs of 512), which caps their registers at 64 (except the batched
 // persistent variant, which would spill); FP64 leaves the register count to
-// the compiler.
+// the compiler, except for one-tile-per-CTA tiles of one node row per thread
+// (k_step_row), which ask for three resident CTAs: they fit in 85 registers
+// without spilling, and the compiler's own choice for the batched variant
+// (94-98) would leave two.
+template <typename T, bool ONE> using ArgsOf = typename std::conditional<ONE, StepArgs<T>, BatchArgs>::type;
+
 template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
-__global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, const int4* __restrict__ tiles,
-                                             int ntiles, int parity, unsigned long long timeout_ns,
-                                             const __grid_constant__ StepArgs<T> one) {
-    step_body<T, BX, BY, NT, NBUF, ONE>(insts, tiles, ntiles, parity, timeout_ns, one);
+__global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, int ntiles, int parity,
+                                             unsigned long long timeout_ns,
+                                             const __grid_constant__ ArgsOf<T, ONE> args) {
+    step_body<T, BX, BY, NT, NBUF, ONE>(insts, ntiles, parity, timeout_ns, args);
+}
+template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
+__global__ void __launch_bounds__(NT, 3) k_step_row(const Inst* __restrict__ insts, int ntiles, int parity,
+                                                    unsigned long long timeout_ns,
+                                                    const __grid_constant__ ArgsOf<T, ONE> args) {
+    step_body<T, BX, BY, NT, NBUF, ONE>(insts, ntiles, parity, timeout_ns, args);
 }
 template <int BX, int BY, int NT, int NBUF, bool ONE>
 __global__ void __launch_bounds__(NT, (ONE || NBUF == 1) ? 1024 / NT : 1) k_step_f32(const Inst* __restrict__ insts,
-                                                            const int4* __restrict__ tiles, int ntiles, int parity,
-                                                            unsigned long long timeout_ns,
-                                                            const __grid_constant__ StepArgs<float> one) {
-    step_body<float, BX, BY, NT, NBUF, ONE>(insts, tiles, ntiles, parity, timeout_ns, one);
+                                                            int ntiles, int parity, unsigned long long timeout_ns,
+                                                            const __grid_constant__ ArgsOf<float, ONE> args) {
+    step_body<float, BX, BY, NT, NBUF, ONE>(insts, ntiles, parity, timeout_ns, args);
 }
 // the kernel a (precision, ONE) launch uses
-template <typename T, int BX, int BY, int NT, int NBUF, bool ONE> struct KSel {
+template <typename T, int BX, int BY, int NT, int NBUF, bool ONE,
+          int KIND = std::is_same<T, float>::value ? 2 : (BX * BY == NT && NBUF == 1 ? 1 : 0)>
+struct KSel {
     static constexpr auto fn = &k_step<T, BX, BY, NT, NBUF, ONE>;
 };
-template <int BX, int BY, int NT, int NBUF, bool ONE> struct KSel<float, BX, BY, NT, NBUF, ONE> {
+template <typename T, int BX, int BY, int NT, int NBUF, bool ONE> struct KSel<T, BX, BY, NT, NBUF, ONE, 1> {
+    static constexpr auto fn = &k_step_row<T, BX, BY, NT, NBUF, ONE>;
+};
+template <typename T, int BX, int BY, int NT, int NBUF, bool ONE> struct KSel<T, BX, BY, NT, NBUF, ONE, 2> {
     static constexpr auto fn = &k_step_f32<BX, BY, NT, NBUF, ONE>;
 };
 
@@ -508,18 +569,17 @@ template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
         cudaError_t e = prep_one<false>();
         return e != cudaSuccess ? e : prep_one<true>();
     }
-    static cudaError_t launch(const Inst* d, const int4* t, int n, int parity, unsigned long long to, const void* one,
+    static cudaError_t launch(const Inst* d, const void* args, bool one, int n, int parity, unsigned long long to,
                               cudaStream_t st) {
         // one CTA per tile, or a persistent grid of resident CTAs striding over the tiles
         const int cap = grid_cap[one ? 1 : 0];
         const int grid = NBUF == 1 ? n : (n < cap ? n : cap);
-        if (one) {
-            KSel<T, BX, BY, NT, NBUF, true>::fn<<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to,
-                                                                            *static_cast<const StepArgs<T>*>(one));
-        } else {
-            static const StepArgs<T> none{};
-            KSel<T, BX, BY, NT, NBUF, false>::fn<<<grid, NT, Gm::smem, st>>>(d, t, n, parity, to, none);
-        }
+        if (one)
+            KSel<T, BX, BY, NT, NBUF, true>::fn<<<grid, NT, Gm::smem, st>>>(d, n, parity, to,
+                                                                            *static_cast<const StepArgs<T>*>(args));
+        else
+            KSel<T, BX, BY, NT, NBUF, false>::fn<<<grid, NT, Gm::smem, st>>>(d, n, parity, to,
+                                                                             *static_cast<const BatchArgs*>(args));
         return cudaGetLastError();
     }
 };
@@ -529,7 +589,7 @@ struct Entry {
     TileCfg (*tc)();
     size_t (*smem)();
     cudaError_t (*prepare)();
-    cudaError_t (*launch)(const Inst*, const int4*, int, int, unsigned long long, const void*, cudaStream_t);
+    cudaError_t (*launch)(const Inst*, const void*, bool, int, int, unsigned long long, cudaStream_t);
     int nbuf;
 };
 
@@ -582,11 +642,11 @@ cudaError_t step_prepare(int prec, int k) {
     return e[k].prepare();
 }
 
-cudaError_t step_launch(int prec, int k, const Inst* d_insts, const int4* d_tiles, int ntiles, int parity,
-                        unsigned long long timeout_ns, const void* one, cudaStream_t st) {
+cudaError_t step_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int parity,
+                        unsigned long long timeout_ns, cudaStream_t st) {
     int n;
     const Entry* e = table(prec, &n);
-    return e[k].launch(d_insts, d_tiles, ntiles, parity, timeout_ns, one, st);
+    return e[k].launch(d_insts, args, one, ntiles, parity, timeout_ns, st);
 }
 
 }  // namespace lbm

@@ -6,10 +6,11 @@ least-squares fit runs in liblbm.so.  Two drivers:
 - ``laplace_sweep``: static droplets of several radii for each (T/Tc, kappa);
   sigma is the slope of Delta p against 1/R_eq (Laplace's law, Eq. 22), with
   the coexistence densities and the peak spurious velocity per instance.
-- ``batched_sweep``: uneven square domains stepped together in one launch per
-  step (a tile table over all instances, CUDA-graph replay, tile shape and
-  CTA schedule picked by ``lbm_autotune``), timed against running the same
-  instances one after another.
+- ``batched_sweep``: uneven square domains stepped together, one launch per
+  step for up to 64 instances (their tensor maps and tile counts in the
+  kernel's argument block, CUDA-graph replay, tile shape and CTA schedule
+  picked by ``lbm_autotune``), timed against running the same instances one
+  after another.
 
 Run as ``python -m paper_1412_7228_gb300.sweep --help``.
 """

@@ -112,7 +112,7 @@ def test_bench_configuration_conserves_mass(setup):
 @pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 1e-14)])
 def test_batched_sweep_configuration_matches_oracle_on_sampled_windows(setup, prec, tol):
     """The 64 uneven droplets of the batched sweep (L in {128, ..., 1024},
-    seed 7228) in one tile-table launch, tile shape autotuned and graphs on
+    seed 7228) in one batched launch, tile shape autotuned and graphs on
     as the sweep runs them: 3 steps, then three oracle windows per instance
     (on the interface, across the wrapped corner, at a seeded place).
     Error: max |rho - rho_oracle| over a window / max rho_oracle there.  A

@@ -207,6 +207,35 @@ def test_batch_equals_separate_runs(P):
                 assert np.array_equal(outs[i], solo[i]), (prec, sched, i)
 
 
+def test_batch_of_more_than_64_instances(P):
+    """A batch beyond one launch's 64 instances (70 uneven lattices: two
+    launches per step) gives every instance the bits it gets alone, for each
+    CTA schedule, in the one-tile-per-CTA and the persistent tile shapes, with
+    CUDA graphs, and counts two kernel launches per step."""
+    eos, op, rg, rl = cs_case(P)
+    rng = np.random.default_rng(70)
+    shapes = [(int(rng.integers(16, 48)), int(rng.integers(24, 56))) for _ in range(70)]
+    rhos = [I.droplet_density(nx, ny, min(nx, ny) / 4, rl, rg) for nx, ny in shapes]
+    steps = 40
+    solo = [gpu_run(P, P.LBM_FP32, eos, op, r, steps, rho_ref=rg) for r in rhos]
+    persistent = [k for k, c in enumerate(P.lbm_tile_configs(P.LBM_FP32)) if c[3] == 2]
+    for cfg in (0, persistent[0]):
+        for sched in (0, 1, 2):
+            b = P.Batch([s[0] for s in shapes], [s[1] for s in shapes], P.LBM_FP32)
+            b.set_schedule(cfg, sched)
+            for i, r in enumerate(rhos):
+                b.set_params(i, eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+                b.init_density(i, r)
+            b.use_graphs(True)
+            n0 = b.kernel_launches()
+            b.step(steps)
+            assert b.kernel_launches() - n0 == 2 * steps
+            outs = [b.read_populations(i) for i in range(len(shapes))]
+            b.close()
+            for i in range(len(shapes)):
+                assert np.array_equal(outs[i], solo[i]), (cfg, sched, i)
+
+
 def test_checkpoint_resume_is_bit_identical(P, tmp_path):
     eos, op, rg, rl = cs_case(P)
     rho0 = I.droplet_density(70, 50, 12, rl, rg)
