@@ -227,9 +227,9 @@ def test_batch_of_more_than_64_instances(P):
                 b.set_params(i, eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
                 b.init_density(i, r)
             b.use_graphs(True)
-            n0 = b.kernel_launches()
+            n0 = b.kernel_launches
             b.step(steps)
-            assert b.kernel_launches() - n0 == 2 * steps
+            assert b.kernel_launches - n0 == 2 * steps
             outs = [b.read_populations(i) for i in range(len(shapes))]
             b.close()
             for i in range(len(shapes)):
