@@ -93,6 +93,17 @@ int lbm_eos_maxwell(const lbm_eos* eos, double* rho_g, double* rho_l, double* p0
 int lbm_laplace_fit(int n, const double* dp, const double* R, double* sigma, double* icpt,
                     double* r2);
 
+/* Self-check of the FP64 step's reciprocal, division and square root (two
+ * Newton-Raphson, resp. Goldschmidt, steps from the hardware estimates)
+ * against IEEE-rounded 1/d, a/d and sqrt(d) on the current device: n values
+ * of d spread evenly over [lo, hi], numerators a in [0.37, 0.87).  Writes
+ * result[0..2] = the largest distances in units in the last place (rcp, div,
+ * sqrt) and result[3] = 1 when sqrt(+0) = +0, sqrt(-0) = -0 and sqrt(-1) is
+ * NaN.  Synchronous (legacy default stream).  LBM_EINVAL unless
+ * 0 < lo < hi < inf, n >= 1 and result != NULL; LBM_ECUDA on a device
+ * error. */
+int lbm_fp64_math_check(double lo, double hi, long long n, unsigned long long result[4]);
+
 /* ---- Context ------------------------------------------------------------ */
 
 /* Bytes of device memory one context of these lattices needs when the caller

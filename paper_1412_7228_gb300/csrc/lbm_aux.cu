@@ -250,6 +250,42 @@ int grid_for(long long n) {
     return static_cast<int>(b);
 }
 
+// ---- the FP64 step's division, reciprocal and square root against IEEE --
+// Distance in units in the last place; values of opposite sign or NaN count
+// as infinitely far.
+__device__ __forceinline__ unsigned long long ulp_distance(double a, double b) {
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    if (x == y) return 0;
+    if (!(a == a) || !(b == b) || ((x ^ y) < 0)) return ~0ull;
+    return static_cast<unsigned long long>(x > y ? x - y : y - x);
+}
+
+// out[0..2]: largest distance of Fast<double>::rcp(d), div(a, d), sqrt(d)
+// from 1/d, a/d, sqrt(d) (IEEE-rounded: this file keeps nvcc's default
+// -prec-div and -prec-sqrt) over n values of d spread evenly over [lo, hi],
+// a in [0.37, 0.87); out[3] = 1 if sqrt keeps +0, -0 and gives NaN for -1.
+__global__ void k_math_check(long long n, double lo, double hi, unsigned long long* out) {
+    unsigned long long m0 = 0, m1 = 0, m2 = 0;
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        const double d = lo + (hi - lo) * (static_cast<double>(i) / static_cast<double>(n));
+        const double a = 0.37 + 0.5 * static_cast<double>((i * 2654435761ll) & 0xffff) / 65536.0;
+        m0 = max(m0, ulp_distance(Fast<double>::rcp(d), 1.0 / d));
+        m1 = max(m1, ulp_distance(Fast<double>::div(a, d), a / d));
+        m2 = max(m2, ulp_distance(Fast<double>::sqrt(d), sqrt(d)));
+    }
+    atomicMax(&out[0], m0);
+    atomicMax(&out[1], m1);
+    atomicMax(&out[2], m2);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double pz = Fast<double>::sqrt(0.0), nz = Fast<double>::sqrt(-0.0), neg = Fast<double>::sqrt(-1.0);
+        out[3] = (__double_as_longlong(pz) == 0 && __double_as_longlong(nz) == __double_as_longlong(-0.0) &&
+                  !(neg == neg))
+                     ? 1ull
+                     : 0ull;
+    }
+}
+
 }  // namespace
 
 cudaError_t aux_init(const Inst& h, const Inst* d, const double* rho, const double* ux, const double* uy,
@@ -311,6 +347,11 @@ cudaError_t aux_stats(const Inst& h, const Inst* d, int parity, double* partials
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_finish<<<1, 32, 0, st>>>(partials, kReduceBlocks, 4, result);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_math_check(long long n, double lo, double hi, unsigned long long* out) {
+    k_math_check<<<1024, kThreads>>>(n, lo, hi, out);
     return cudaGetLastError();
 }
 

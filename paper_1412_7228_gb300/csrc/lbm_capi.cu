@@ -598,6 +598,24 @@ int lbm_eos_maxwell(const lbm_eos* eos, double* rho_g, double* rho_l, double* p0
     return LBM_OK;
 }
 
+int lbm_fp64_math_check(double lo, double hi, long long n, unsigned long long result[4]) {
+    if (!result || n < 1 || !(lo > 0.0) || !(hi > lo) || !std::isfinite(hi)) return LBM_EINVAL;
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ECUDA;
+    }
+    int rc = LBM_OK;
+    if (cudaMemset(d, 0, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        lbm::aux_math_check(n, lo, hi, d) != cudaSuccess ||
+        cudaMemcpy(result, d, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        rc = LBM_ECUDA;
+    }
+    cudaFree(d);
+    return rc;
+}
+
 int lbm_laplace_fit(int n, const double* dp, const double* R, double* sigma, double* icpt, double* r2) {
     if (n < 2 || !dp || !R) return LBM_EINVAL;
     double sx = 0, sy = 0, sxx = 0, sxy = 0;

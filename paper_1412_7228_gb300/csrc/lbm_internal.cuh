@@ -147,6 +147,51 @@ template <typename T> __device__ __forceinline__ T psi_radicand(const Phys<T>& P
     return P.two_over_G * (p_eos(P, rho) - rho * T(1.0 / 3.0));
 }
 
+// Division, reciprocal and square root of the fused step.  FP32 uses the
+// hardware approximations (a couple of ulp, far inside the FP32 error budget
+// of the stored populations).  FP64 refines the hardware estimates
+// (rcp.approx / rsqrt.approx, accurate to about 2^-22) with two steps of a
+// quadratically converging iteration, which leaves only the rounding of the
+// last step: 1/d by Newton-Raphson (e = 1 - d r, r <- r + r e), sqrt(x) by
+// Goldschmidt's coupled iteration (g -> sqrt(x), h -> 1/(2 sqrt(x)):
+// r = 1/2 - g h, g <- g + g r, h <- h + h r).  Both stay within 1 ulp of the
+// IEEE-rounded 1/d and sqrt(x), a * rcp(d) within 1 ulp of a/d
+// (lbm_fp64_math_check measures this on the device); they take fewer FP64
+// operations than the IEEE sequences, and the FP64 step is bound by its FP64
+// pipe.  sqrt keeps sqrt(+-0) = +-0 and NaN for x < 0.
+template <typename T> struct Fast;
+template <> struct Fast<float> {
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
+    static __device__ __forceinline__ float sqrt(float a) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
+};
+template <> struct Fast<double> {
+    static __device__ __forceinline__ double rcp(double d) {
+        double r;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+        double e = fma(-d, r, 1.0);
+        r = fma(r, e, r);
+        e = fma(-d, r, 1.0);
+        return fma(r, e, r);
+    }
+    static __device__ __forceinline__ double div(double a, double b) { return a * rcp(b); }
+    static __device__ __forceinline__ double sqrt(double x) {
+        double y;
+        asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+        double g = x * y, h = 0.5 * y;
+        double r = fma(-g, h, 0.5);
+        g = fma(g, r, g);
+        h = fma(h, r, h);
+        r = fma(-g, h, 0.5);
+        g = fma(g, r, g);
+        return (__double_as_longlong(x) << 1) == 0 ? x : g;   // +-0: rsqrt is infinite there
+    }
+};
+
 // ---- PTX helpers --------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -233,6 +278,8 @@ cudaError_t aux_gather_plane(const Inst& host, const Inst* d_inst, int parity, i
 // field: 0 rho, 1 ux, 2 uy, 3 psi
 cudaError_t aux_field(const Inst& host, const Inst* d_inst, int parity, int field, double* out,
                       cudaStream_t st);
+// out: 4 device words (see lbm_fp64_math_check); default stream.
+cudaError_t aux_math_check(long long n, double lo, double hi, unsigned long long* out);
 constexpr int kReduceBlocks = 304;   // 2 CTAs per SM of a 152-SM GB300: partial sums of FP64 reductions
 constexpr int kReduceSlots = 8;
 cudaError_t aux_measure(const Inst& host, const Inst* d_inst, int parity, double cx, double cy,

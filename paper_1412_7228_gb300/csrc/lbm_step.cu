@@ -71,30 +71,6 @@ template <typename T> __device__ __forceinline__ T rho_dev(const T (&f)[9]) {
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-// Moment-space collision of one node in deviation form (Eqs. 2-6, 25, 26).
-// Every expression maps onto itself (or its negative) under the mirrors
-// above, which keeps symmetric states symmetric to the last bit.
-// f: pre-collision f_a - t_a rho_ref; out: post-collision, same form.
-// Division, reciprocal and square root of the step.  FP32 uses the
-// hardware approximations (a couple of ulp, far inside the FP32 error
-// budget of the stored populations); FP64 keeps IEEE operations.
-template <typename T> struct Fast;
-template <> struct Fast<float> {
-    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-    static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
-    static __device__ __forceinline__ float sqrt(float a) {
-        float r;
-        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
-        return r;
-    }
-};
-template <> struct Fast<double> {
-    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
-    static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
-    static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
-};
-
-
 // The parameters one node needs, copied into registers once per tile (the
 // descriptor lives in global memory, and the compiler may not keep values
 // read through it across the node loop's stores).
@@ -114,6 +90,10 @@ template <typename T> struct RegsSel { using type = RegsOf<T, const T&>; };
 template <> struct RegsSel<float> { using type = RegsOf<float, float>; };
 template <typename T> using Regs = typename RegsSel<T>::type;
 
+// Moment-space collision of one node in deviation form (Eqs. 2-6, 25, 26).
+// Every expression maps onto itself (or its negative) under the mirrors
+// above, which keeps symmetric states symmetric to the last bit.
+// f: pre-collision f_a - t_a rho_ref; out: post-collision, same form.
 // P: the relaxation constants (register copies for FP32, references into the
 // descriptor for FP64).
 template <typename T, typename RP>

@@ -29,7 +29,7 @@ _CODES = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA", LBM_EU
           LBM_ETIMEOUT: "ETIMEOUT", LBM_EIO: "EIO"}
 
 EXPORTS = [
-    "lbm_eos_pressure", "lbm_eos_critical", "lbm_eos_maxwell", "lbm_laplace_fit",
+    "lbm_eos_pressure", "lbm_eos_critical", "lbm_eos_maxwell", "lbm_laplace_fit", "lbm_fp64_math_check",
     "lbm_required_bytes", "lbm_batch_required_bytes", "lbm_create", "lbm_batch_create", "lbm_destroy",
     "lbm_set_params", "lbm_batch_set_params", "lbm_set_viscosity", "lbm_batch_set_viscosity",
     "lbm_init_density", "lbm_batch_init_density",
@@ -90,6 +90,8 @@ def lib():
     sig = {
         "lbm_eos_pressure": ([E, ctypes.c_double, _dp], ctypes.c_int),
         "lbm_eos_critical": ([E, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_fp64_math_check": ([ctypes.c_double, ctypes.c_double, ctypes.c_longlong,
+                                 ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
         "lbm_eos_maxwell": ([E, _dp, _dp, _dp], ctypes.c_int),
         "lbm_laplace_fit": ([ctypes.c_int, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
         "lbm_required_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
@@ -205,6 +207,15 @@ def lbm_laplace_fit(dp: Sequence[float], R: Sequence[float]):
     _check(None, lib().lbm_laplace_fit(len(dp), _ptr(dp), _ptr(R), ctypes.byref(s), ctypes.byref(c),
                                        ctypes.byref(r2)))
     return s.value, c.value, r2.value
+
+
+def lbm_fp64_math_check(lo: float, hi: float, n: int) -> dict:
+    """Largest distance in ulp of the FP64 step's reciprocal, division and
+    square root from IEEE-rounded results over n arguments in [lo, hi], and
+    whether sqrt keeps +-0 and gives NaN below zero (runs on the device)."""
+    r = (ctypes.c_ulonglong * 4)()
+    _check(None, lib().lbm_fp64_math_check(lo, hi, n, r))
+    return {"rcp_ulp": int(r[0]), "div_ulp": int(r[1]), "sqrt_ulp": int(r[2]), "sqrt_special_ok": bool(r[3])}
 
 
 LBM_STATIC_MAX_NODES = 16777216
