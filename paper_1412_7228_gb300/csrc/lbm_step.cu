@@ -341,21 +341,42 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
         }
 
         // ---- rho and psi of the tile and its ring (Eq. 10) ---------------
+        // A density outside the EOS's psi domain gives a negative radicand and
+        // a NaN psi (square root), which reaches every output of the owned
+        // node (F and Q are linear in psi, 0 x NaN is NaN): the collision's
+        // NaN check below records it.  Ring nodes beyond the lattice's
+        // ghost images feed no owned node.
         if (interact && ok) {
             auto ring = [&](int i, int j) {
                 const T* q = sf + (j + 1) * Gm::WB + (i + Gm::HX - 1);
                 T g[9];
 #pragma unroll
                 for (int a = 0; a < 9; ++a) g[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
-                const T rad = radicand_step(E, rho_ref + rho_dev(g));
-                sp[j * Gm::WP + i] = Fast<T>::sqrt(rad);
-                if (!(rad >= T(0)) && i >= 1 && i <= BX && j >= 1 && j <= BY && x0 - 1 + i < nx &&
-                    y0 - 1 + j < ny)
-                    bad = true;
+                sp[j * Gm::WP + i] = Fast<T>::sqrt(radicand_step(E, rho_ref + rho_dev(g)));
             };
-            for (int j = ty; j < Gm::HP; j += Gm::TY) ring(tx, j);
-            // the ring's two right-hand columns, spread over the first threads
-            for (int e = tid; e < 2 * Gm::HP; e += NT) ring(BX + (e & 1), e >> 1);
+            // rows ty, ty + TY, ... (unrolled where a thread owns several rows;
+            // the one-row shapes run under a tighter register bound); the two
+            // right-hand ring columns go to the threads the last row pass
+            // leaves idle when there are enough, so that no warp evaluates
+            // more ring nodes than the busiest row pass gives it
+            constexpr int K = (Gm::HP + Gm::TY - 1) / Gm::TY;
+            constexpr bool kMerge = Gm::ROWS > 1 && (K * Gm::TY - Gm::HP) * BX >= 2 * Gm::HP;
+            if constexpr (Gm::ROWS > 1) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int j = ty + k * Gm::TY;
+                    if (j < Gm::HP) {
+                        ring(tx, j);
+                    } else if (kMerge && k == K - 1) {
+                        const int e = (j - Gm::HP) * BX + tx;
+                        if (e < 2 * Gm::HP) ring(BX + (e & 1), e >> 1);
+                    }
+                }
+            } else {
+                for (int j = ty; j < Gm::HP; j += Gm::TY) ring(tx, j);
+            }
+            if (!kMerge)
+                for (int e = tid; e < 2 * Gm::HP; e += NT) ring(BX + (e & 1), e >> 1);
         }
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
