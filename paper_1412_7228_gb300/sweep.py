@@ -77,14 +77,17 @@ def _harvest(batch: L.Batch, i: int, d: Droplet, r_out_gap: float = 10.0):
 
 
 def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP32, autotune: bool = True,
-              graphs: bool = True, s=S_DEFAULT) -> Dict:
-    """Step every droplet together; fill in the per-droplet results."""
+              graphs: bool = True, s=S_DEFAULT, schedule: Optional[Tuple[int, int]] = None) -> Dict:
+    """Step every droplet together; fill in the per-droplet results.
+    schedule: (tile configuration, CTA schedule) instead of autotuning."""
     import torch
     batch = L.Batch([d.L for d in droplets], [d.L for d in droplets], precision)
     for i, d in enumerate(droplets):
         _setup(batch, i, d, s)
     tune = None
-    if autotune:
+    if schedule is not None:
+        batch.set_schedule(*schedule)
+    elif autotune:
         tune = batch.autotune(5)
     if graphs:
         batch.use_graphs(True)
@@ -172,6 +175,12 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="batched droplet sweeps on the GPU")
     ap.add_argument("--laplace", action="store_true", help="Laplace-law sweep (256^2, 5 radii x 4 kappa x 3 T)")
     ap.add_argument("--batched", action="store_true", help="64 uneven instances, batched vs sequential")
+    ap.add_argument("--uniform", type=int, default=None, metavar="L",
+                    help="time --n droplets of L^2 (R0 = 0.2 L, 0.7 Tc, A = -0.85, kappa = 0.3) stepped together, "
+                         "with --tile/--schedule instead of autotuning and without graphs (one launch per step "
+                         "and 64 instances, as a profiler sees them)")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--schedule", type=int, default=0)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--n", type=int, default=64)
@@ -182,6 +191,14 @@ def main(argv=None):
         out = {"sweep": "laplace", "precision": args.precision, "seconds": info["seconds"], "mlups": info["mlups"],
                "fits": [f.__dict__ for f in fits], "droplets": info.get("droplets")}
         print(json.dumps(out))
+    if args.uniform:
+        steps = args.steps or 40
+        drops = [Droplet(args.uniform, 0.2 * args.uniform, 0.7, -0.85, 0.3) for _ in range(args.n)]
+        r = run_batch(drops, steps, prec, graphs=False, schedule=(args.tile, args.schedule))
+        print(json.dumps({"sweep": "uniform", "instances": args.n, "L": args.uniform, "steps": steps,
+                          "precision": args.precision, "tile": args.tile, "schedule": args.schedule,
+                          "seconds": r["seconds"], "mlups": r["mlups"], "launches": r["launches"],
+                          "unstable": sum(d.status != 0 for d in drops)}))
     if args.batched:
         steps = args.steps or 20000
         drops = sweep_droplets(args.n)
