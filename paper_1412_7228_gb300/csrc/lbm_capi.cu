@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbm_internal.cuh"
@@ -213,7 +214,8 @@ struct lbm_ctx {
     std::vector<Maps> maps;
     // a batch (n > 1) is stepped by one launch per chunk of up to
     // kBatchLaunchMax instances: argument blocks per time-level parity
-    std::vector<lbm::BatchArgs> bargs[2];
+    std::vector<lbm::BatchArgs<float>> bargs_f[2];
+    std::vector<lbm::BatchArgs<double>> bargs_d[2];
     std::vector<int> chunk_tiles;
     int* d_status = nullptr;
     double* d_partials = nullptr;
@@ -306,8 +308,30 @@ template <typename T> void fill_one(lbm_ctx* c, lbm::StepArgs<T>& a, const lbm::
     a.tiles_x = (I.nx + lbm::step_config(c->prec, c->cfg).bx - 1) / lbm::step_config(c->prec, c->cfg).bx;
 }
 
-void refresh_one(lbm_ctx* c) {
-    if (c->n != 1) return;
+// The per-instance part of a batched argument block: array addresses and
+// sizes, and in FP32 the constants (FP64 kernels read those from the
+// descriptors).
+template <typename T> void fill_slots(const lbm_ctx* c, lbm::BatchArgs<T>& a) {
+    for (int k = 0; k < a.n; ++k) {
+        const Inst& I = c->h[a.inst[k]];
+        a.lat[k].pop[0] = I.pop[0];
+        a.lat[k].pop[1] = I.pop[1];
+        a.lat[k].status = I.status;
+        a.lat[k].plane = I.plane;
+        a.lat[k].nx = I.nx;
+        a.lat[k].ny = I.ny;
+        a.lat[k].pitch = I.pitch;
+        if constexpr (std::is_same<T, float>::value) a.phys.P[k] = I.pf;
+    }
+}
+
+// Argument blocks after a change of an instance's parameters.
+void refresh_args(lbm_ctx* c) {
+    if (c->n != 1) {
+        for (auto& v : c->bargs_f)
+            for (auto& a : v) fill_slots(c, a);
+        return;
+    }
     fill_one(c, c->one_f, c->h[0].pf);
     fill_one(c, c->one_d, c->h[0].pd);
 }
@@ -322,28 +346,13 @@ const void* one_args(lbm_ctx* c) {
 // each chunk's instances interleaved through a tile table, 2: most tiles
 // first) and cut into chunks of kBatchLaunchMax; a chunk's tiles run in slot
 // order, row-major within an instance, unless it has a tile table.
-int build_tiles(lbm_ctx* c) {
-    const lbm::TileCfg t = lbm::step_config(c->prec, c->cfg);
-    std::vector<int> tx(c->n), cnt(c->n);
-    size_t total = 0;
-    for (int i = 0; i < c->n; ++i) {
-        tx[i] = (c->nx[i] + t.bx - 1) / t.bx;
-        cnt[i] = tx[i] * ((c->ny[i] + t.by - 1) / t.by);
-        total += static_cast<size_t>(cnt[i]);
-    }
-    if (total > c->L.tiles_cap || total > 0x7fffffff) return fail(c, LBM_ENOMEM, "tile table larger than reserved%s");
-    c->ntiles = static_cast<int>(total);
-    for (auto& v : c->bargs) v.clear();
-    c->chunk_tiles.clear();
-    if (c->n == 1) return LBM_OK;   // one lattice: StepArgs, tiles from blockIdx
-
-    std::vector<int> order(c->n);
-    for (int i = 0; i < c->n; ++i) order[i] = i;
-    if (c->sched == 2) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
-    std::vector<int4> table;   // schedule 1: every chunk's table, one after another
+template <typename T>
+int build_chunks(lbm_ctx* c, std::vector<lbm::BatchArgs<T>> (&out)[2], const std::vector<int>& order,
+                 const std::vector<int>& tx, const std::vector<int>& cnt, const lbm::TileCfg& t,
+                 std::vector<int4>& table) {
     for (int c0 = 0; c0 < c->n; c0 += lbm::kBatchLaunchMax) {
         const int m = std::min(lbm::kBatchLaunchMax, c->n - c0);
-        lbm::BatchArgs a;
+        lbm::BatchArgs<T> a;
         std::memset(&a, 0, sizeof a);
         a.n = m;
         int first = 0;
@@ -359,6 +368,7 @@ int build_tiles(lbm_ctx* c) {
             first += cnt[i];
         }
         a.first[m] = first;
+        fill_slots(c, a);
         if (c->sched == 1) {
             a.tiles = c->d_tiles + table.size();
             int most = 0;
@@ -370,10 +380,36 @@ int build_tiles(lbm_ctx* c) {
         }
         for (int par = 0; par < 2; ++par) {
             for (int k = 0; k < m; ++k) a.tmap[k] = c->maps[a.inst[k]].tmap[par];
-            c->bargs[par].push_back(a);
+            out[par].push_back(a);
         }
         c->chunk_tiles.push_back(first);
     }
+    return LBM_OK;
+}
+
+int build_tiles(lbm_ctx* c) {
+    const lbm::TileCfg t = lbm::step_config(c->prec, c->cfg);
+    std::vector<int> tx(c->n), cnt(c->n);
+    size_t total = 0;
+    for (int i = 0; i < c->n; ++i) {
+        tx[i] = (c->nx[i] + t.bx - 1) / t.bx;
+        cnt[i] = tx[i] * ((c->ny[i] + t.by - 1) / t.by);
+        total += static_cast<size_t>(cnt[i]);
+    }
+    if (total > c->L.tiles_cap || total > 0x7fffffff) return fail(c, LBM_ENOMEM, "tile table larger than reserved%s");
+    c->ntiles = static_cast<int>(total);
+    for (auto& v : c->bargs_f) v.clear();
+    for (auto& v : c->bargs_d) v.clear();
+    c->chunk_tiles.clear();
+    if (c->n == 1) return LBM_OK;   // one lattice: StepArgs, tiles from blockIdx
+
+    std::vector<int> order(c->n);
+    for (int i = 0; i < c->n; ++i) order[i] = i;
+    if (c->sched == 2) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
+    std::vector<int4> table;   // schedule 1: every chunk's table, one after another
+    const int rc = c->prec == LBM_FP32 ? build_chunks(c, c->bargs_f, order, tx, cnt, t, table)
+                                       : build_chunks(c, c->bargs_d, order, tx, cnt, t, table);
+    if (rc) return rc;
     if (!table.empty()) {
         CK(c, cudaMemcpyAsync(c->d_tiles, table.data(), table.size() * sizeof(int4), cudaMemcpyHostToDevice,
                               c->stream));
@@ -390,8 +426,10 @@ cudaError_t launch_step(lbm_ctx* c, int parity) {
         return lbm::step_launch(c->prec, c->cfg, c->d_inst, one_args(c), true, c->ntiles, parity, kTimeoutNs,
                                 c->stream);
     for (size_t j = 0; j < c->chunk_tiles.size(); ++j) {
-        cudaError_t e = lbm::step_launch(c->prec, c->cfg, c->d_inst, &c->bargs[parity][j], false, c->chunk_tiles[j],
-                                         parity, kTimeoutNs, c->stream);
+        const void* a = c->prec == LBM_FP32 ? static_cast<const void*>(&c->bargs_f[parity][j])
+                                            : static_cast<const void*>(&c->bargs_d[parity][j]);
+        cudaError_t e = lbm::step_launch(c->prec, c->cfg, c->d_inst, a, false, c->chunk_tiles[j], parity, kTimeoutNs,
+                                         c->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -404,7 +442,7 @@ int apply_schedule(lbm_ctx* c, int cfg, int sched) {
     CK(c, lbm::step_prepare(c->prec, cfg));
     int rc = encode_maps(c);
     if (rc) return rc;
-    refresh_one(c);
+    refresh_args(c);
     rc = upload_insts(c);
     if (rc) return rc;
     return build_tiles(c);
@@ -753,7 +791,7 @@ int lbm_batch_set_params(lbm_ctx* c, int i, const lbm_eos* eos, double A, double
     hp.visc_rho_l = keep.visc_rho_l;
     fill_phys(c->h[i].pf, hp);
     fill_phys(c->h[i].pd, hp);
-    refresh_one(c);
+    refresh_args(c);
     drop_graphs(c);
     return upload_insts(c);
 }
@@ -780,7 +818,7 @@ int lbm_batch_set_viscosity(lbm_ctx* c, int i, int enable, double nu_gas, double
     hp.visc_rho_l = rho_liquid;
     fill_phys(c->h[i].pf, hp);
     fill_phys(c->h[i].pd, hp);
-    refresh_one(c);
+    refresh_args(c);
     drop_graphs(c);
     return upload_insts(c);
 }
@@ -1045,7 +1083,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
     }
     std::fclose(fp);
     c->steps = hd.steps;
-    refresh_one(c);
+    refresh_args(c);
     drop_graphs(c);
     CK(c, cudaMemset(c->d_status, 0, c->n * sizeof(int)));
     return upload_insts(c);

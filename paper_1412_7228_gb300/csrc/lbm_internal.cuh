@@ -85,16 +85,30 @@ template <typename T> struct StepArgs {   // CUtensorMap members give it their a
     int nx, ny, pitch, tiles_x;
 };
 
-// What a batched launch needs to find its tiles, passed by value as a
-// __grid_constant__ kernel argument as well: the tensor maps of up to
-// kBatchLaunchMax instances (in parameter space a map needs neither a
-// load of its own nor a tensormap proxy fence, which a map in global memory
-// needs before every first use in a CTA) and their tile counts.  Slot k's
-// tiles are first[k] .. first[k+1]-1, row-major over tiles_x[k] columns;
-// with a tile table (the interleaved schedule) entry t gives (slot, x0, y0)
-// instead.  A batch with more instances is stepped by several launches.
+// What a batched launch needs, passed by value as a __grid_constant__
+// kernel argument as well: for up to kBatchLaunchMax instances their tensor
+// maps (in parameter space a map needs neither a load of its own nor a
+// tensormap proxy fence, which a map in global memory needs before every
+// first use in a CTA) and tile counts; in FP32 also their array addresses,
+// sizes and constants, so that the FP32 step reads nothing but populations
+// from global memory (FP64, bound by its FP64 pipe, reads those from the
+// instance descriptors: 64 FP64 constant sets would not fit the 32 KB
+// argument space).  Slot k's tiles are first[k] .. first[k+1]-1, row-major
+// over tiles_x[k] columns; with a tile table (the interleaved schedule)
+// entry t gives (slot, x0, y0) instead.  A batch with more instances is
+// stepped by several launches.
 constexpr int kBatchLaunchMax = 64;
-struct BatchArgs {
+struct SlotLattice {                     // the fields of Inst the step uses
+    void* pop[2];
+    int* status;
+    long long plane;
+    int nx, ny, pitch, pad_;
+};
+template <typename T> struct BatchPhys {};
+template <> struct BatchPhys<float> {
+    Phys<float> P[kBatchLaunchMax];
+};
+template <typename T> struct BatchArgs {
     CUtensorMap tmap[kBatchLaunchMax];   // maps of the source time level of slot k
     const int4* tiles;                   // tile table, or nullptr: tiles in slot order
     int first[kBatchLaunchMax + 1];      // first tile of slot k; first[n] = tiles of the launch
@@ -103,6 +117,8 @@ struct BatchArgs {
     int div_s[kBatchLaunchMax];
     int inst[kBatchLaunchMax];           // slot k -> index into the Inst array
     int n;                               // slots in use, 1..kBatchLaunchMax
+    SlotLattice lat[kBatchLaunchMax];    // read by FP32 launches
+    BatchPhys<T> phys;                   // FP32 only
 };
 
 // floor(r / d) for 0 <= r < 2^31 and d >= 1 as one 64-bit multiply and a
@@ -263,9 +279,9 @@ int step_config_count(int prec);
 TileCfg step_config(int prec, int k);
 size_t step_smem_bytes(int prec, int k);
 cudaError_t step_prepare(int prec, int k);   // sets the dynamic smem attribute
-// args: a StepArgs<float> / StepArgs<double> for a context of one lattice
-// (one = true; tile coordinates from blockIdx), else a BatchArgs of up to
-// kBatchLaunchMax instances.  ntiles: tiles this launch steps.
+// args: a StepArgs<T> for a context of one lattice (one = true; tile
+// coordinates from blockIdx), else a BatchArgs<T> of up to kBatchLaunchMax
+// instances, T the context's precision.  ntiles: tiles this launch steps.
 cudaError_t step_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int parity,
                         unsigned long long timeout_ns, cudaStream_t st);
 

@@ -232,22 +232,26 @@ __device__ __forceinline__ void force_q(T negGw, T hA, T omA, T kGw, T p0, T p1,
     Qxy = kGw * fma(c, sxy1, hA * sxy2);
 }
 
-// The constants of the lattice a tile belongs to: in the one-lattice
-// argument block (parameter space), or in an instance descriptor in global
-// memory.
-template <typename T> __device__ __forceinline__ const Phys<T>& phys_of(const StepArgs<T>& a, const Inst*) {
+// The constants of the lattice a tile belongs to: in the argument block
+// (parameter space), or for a batched FP64 launch in the instance's
+// descriptor in global memory.
+template <typename T>
+__device__ __forceinline__ const Phys<T>& phys_of(const StepArgs<T>& a, const Inst*, int) {
     return a.P;
 }
-template <typename T> __device__ __forceinline__ const Phys<T>& phys_of(const BatchArgs&, const Inst* I) {
-    return phys<T>(I);
+__device__ __forceinline__ const Phys<float>& phys_of(const BatchArgs<float>& a, const Inst*, int slot) {
+    return a.phys.P[slot];
+}
+__device__ __forceinline__ const Phys<double>& phys_of(const BatchArgs<double>&, const Inst* I, int) {
+    return phys<double>(I);
 }
 
 // One kernel, two ways to find the work, both from a __grid_constant__
 // argument block: ONE = a single lattice (StepArgs: constants and tensor
 // maps; tile coordinates from the tile index); otherwise a BatchArgs over up
-// to kBatchLaunchMax instances (tensor maps and tile counts; the tile's
-// instance by a binary search of the tile counts' prefix sums, or from a tile
-// table; constants from the instance's descriptor in global memory).
+// to kBatchLaunchMax instances (tensor maps, tile counts, array addresses and
+// sizes, FP32 constants; the tile's instance by a binary search of the tile
+// counts' prefix sums, or from a tile table).
 // NBUF = 2 makes the CTAs persistent with a two-stage TMA pipeline: while
 // tile k is collided, the box of tile k+1 streams into the other
 // shared-memory buffer.
@@ -316,14 +320,18 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
         int slot, x0, y0;
         tile_of(t, slot, x0, y0);
         const Inst* I = nullptr;
-        if constexpr (!ONE) I = insts + a.inst[slot];
-        const Phys<T>& P = phys_of<T>(a, I);
+        if constexpr (!ONE && sizeof(T) == 8) I = insts + a.inst[slot];
+        const Phys<T>& P = phys_of(a, I, slot);
         int nx, ny;
         int* status;
         if constexpr (ONE) {
             nx = a.nx;
             ny = a.ny;
             status = a.status;
+        } else if constexpr (sizeof(T) == 4) {
+            nx = a.lat[slot].nx;
+            ny = a.lat[slot].ny;
+            status = a.lat[slot].status;
         } else {
             nx = I->nx;
             ny = I->ny;
@@ -396,6 +404,10 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
             dst = static_cast<T*>(a.pop[parity ^ 1]);
             plane = a.plane;
             pitch = a.pitch;
+        } else if constexpr (sizeof(T) == 4) {
+            dst = static_cast<T*>(a.lat[slot].pop[parity ^ 1]);
+            plane = a.lat[slot].plane;
+            pitch = a.lat[slot].pitch;
         } else {
             dst = static_cast<T*>(I->pop[parity ^ 1]);
             plane = I->plane;
@@ -514,7 +526,7 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
 // (k_step_row), which ask for three resident CTAs: they fit in 85 registers
 // without spilling, and the compiler's own choice for the batched variant
 // (94-98) would leave two.
-template <typename T, bool ONE> using ArgsOf = typename std::conditional<ONE, StepArgs<T>, BatchArgs>::type;
+template <typename T, bool ONE> using ArgsOf = typename std::conditional<ONE, StepArgs<T>, BatchArgs<T>>::type;
 
 template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
 __global__ void __launch_bounds__(NT) k_step(const Inst* __restrict__ insts, int ntiles, int parity,
@@ -580,7 +592,7 @@ template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
                                                                             *static_cast<const StepArgs<T>*>(args));
         else
             KSel<T, BX, BY, NT, NBUF, false>::fn<<<grid, NT, Gm::smem, st>>>(d, n, parity, to,
-                                                                             *static_cast<const BatchArgs*>(args));
+                                                                             *static_cast<const BatchArgs<T>*>(args));
         return cudaGetLastError();
     }
 };
