@@ -85,19 +85,32 @@ def measured_peak():
         return PEAK_FALLBACK_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("lbm_step.cu", "lbm_internal.cuh")
+
+
+def kernel_sources_sha():
+    """First 16 hex digits of the SHA-256 of the step kernel's sources (the
+    kernel file followed by the header it compiles), the key under which a
+    committed ncu figure is valid."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(prec_name, kernel):
     """Measured DRAM bytes per lattice update of the step kernel from the
     committed ncu summary, valid only for the kernel it names and while the
-    kernel source is unchanged (traffic per node does not depend on the
+    kernel sources are unchanged (traffic per node does not depend on the
     domain size once the arrays exceed L2)."""
-    src = os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", "lbm_step.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_sources_sha()
     path = os.path.join(ROOT, "profiles", "step_%s_4096_traffic.txt" % prec_name)
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
     except OSError:
         return None
-    if kv.get("lbm_step_cu_sha256_16") != sha or kv.get("kernel") != kernel:
+    if kv.get("kernel_sources_sha256_16") != sha or kv.get("kernel") != kernel:
         return None
     try:
         return float(kv["bytes_per_update"])
@@ -109,13 +122,12 @@ def fp64_alu_roofline(mlups, kernel):
     """FP64 step against the FP64 pipe: GB300 issues 2 FP64 thread-operations
     per clock per SM; the kernel's FP64 operations per lattice update come
     from the committed ncu summary (valid for the kernel it names, while the
-    kernel source is unchanged)."""
-    src = os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", "lbm_step.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    kernel sources are unchanged)."""
+    sha = kernel_sources_sha()
     path = os.path.join(ROOT, "profiles", "step_fp64_1024_alu.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
-        if kv.get("lbm_step_cu_sha256_16") != sha or kv.get("kernel") != kernel:
+        if kv.get("kernel_sources_sha256_16") != sha or kv.get("kernel") != kernel:
             return None
         ops = float(kv["fp64_ops_per_update"])
     except (OSError, KeyError, ValueError):

@@ -63,16 +63,20 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
 def test_traffic_figure_is_used_only_for_the_profiled_kernel():
     """The committed ncu traffic applies to the kernel it names and only while
-    the kernel source hashes to the value recorded beside it."""
+    the kernel's sources (kernel file and the header it compiles) hash to the
+    value recorded beside it."""
     import hashlib
     sys.path.insert(0, ROOT)
     import bench
-    src = os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", "lbm_step.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("lbm_step.cu", "lbm_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", name), "rb").read())
+    sha = h.hexdigest()[:16]
+    assert bench.kernel_sources_sha() == sha
     path = os.path.join(ROOT, "profiles", "step_fp32_4096_traffic.txt")
     kv = dict(l.strip().split("=", 1) for l in open(path) if "=" in l and not l.startswith("#"))
     got = bench.kernel_traffic("fp32", kv["kernel"])
-    if kv["lbm_step_cu_sha256_16"] == sha:
+    if kv["kernel_sources_sha256_16"] == sha:
         assert got == float(kv["bytes_per_update"]) and 72.0 <= got < 80.0
     else:
         assert got is None
