@@ -202,6 +202,16 @@ def make_lattice(P, nx, ny, prec, rho0, stream=None):
     return lat
 
 
+GRAPH_STEPS = 32   # lbm_step replays a captured graph per 32 steps; a remainder runs as plain launches
+
+
+def graph_use(steps):
+    """How lbm_step(steps) issues its work once graphs are on: the steps that
+    ran from captured graph replays and those that ran as plain launches."""
+    g = steps // GRAPH_STEPS * GRAPH_STEPS
+    return {"graphs": g > 0, "graph_steps": g, "plain_launch_steps": steps - g}
+
+
 def time_steps(torch, lat, steps):
     st = lat.stream
     e0 = torch.cuda.Event(enable_timing=True)
@@ -442,8 +452,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t * 1000.0 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == P.LBM_FP32 else "f64",
             "data": "synthetic",
-            "config": workload_config(nx, ny, args.precision, {"tile": list(tile), "graphs": True,
-                                                       "parallelism": "replicas" if ws > 1 else "single"}),
+            "config": workload_config(nx, ny, args.precision, dict(
+                {"tile": list(tile), "parallelism": "replicas" if ws > 1 else "single"}, **graph_use(args.steps))),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "fp64": fp64, "other_workloads": others, "status_ok": status_ok,
         }
@@ -464,7 +474,8 @@ def main():
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--tile", type=int, default=None,
-                    help="tile configuration index (lbm_tile_config); default 0 (FP32) or 1 (FP64)")
+                    help="tile configuration index (lbm_tile_config); default %d (FP32) or %d (FP64)"
+                         % (TILE_FP32, TILE_FP64))
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -294,20 +294,23 @@ int lbm_mlp_invert_kappa(lbm_mlp* m, const float* t_over_tc, const float* A, con
  * latency-critical loop that must not make an allocation call, which can
  * synchronise the whole device.
  *
- * Same sums as lbm_batch_measure (Eq. 22 sampling, FP64), but over a density
- * field d_rho of nx*ny doubles (row-major, x fastest) that the caller keeps in
- * device memory; out receives LBM_MEASURE_N doubles in host memory {p_in,
- * p_out, rho_in, rho_out, R_eq, mass, n_in, n_out}, with p = p_EOS(rho) of eos.
- * Work runs on `stream` (NULL: legacy default stream), which the call
- * synchronises before it returns.
+ * The same sums as lbm_batch_measure, accumulated in FP64, but over a
+ * density field d_rho of nx*ny doubles (row-major, x fastest) that the caller
+ * keeps in device memory of the current device (make d_rho's device current
+ * before the call); out receives LBM_MEASURE_N doubles in host memory {p_in,
+ * p_out, rho_in, rho_out, R_eq, mass, n_in, n_out}, with p = p_EOS(rho) of
+ * eos.  Work runs on `stream` (NULL: legacy default stream); the call copies
+ * the totals to host memory and synchronises the stream before it returns.
  *
  * It allocates nothing: its scratch is a file-scope device array sized for at
  * most LBM_STATIC_MAX_NODES nodes (about 128 KiB, held by every GPU that loads
- * the library until the process exits).  Larger fields are rejected with
- * LBM_EINVAL before any GPU work.  The first call on a device looks up the
- * array's device address with that device current; make that first call
- * before any stream capture.  Every call reuses the same array, so calls
- * whose work overlaps on the GPU (other streams, other host threads) race.
+ * the library until the process exits).  Larger fields, a d_rho that is not
+ * device memory of the current device, and an equation of state or
+ * temperature that lbm_set_params would reject are refused with LBM_EINVAL
+ * before any GPU work.  The first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  Every call reuses the same array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race.
  * Returns LBM_OK, LBM_EINVAL or LBM_ECUDA. */
 #define LBM_STATIC_MAX_NODES 16777216
 int lbm_field_pressure_jump_static(const double* d_rho, int nx, int ny, const lbm_eos* eos, double cx,

@@ -114,17 +114,39 @@ def _roots_at(p: Params, p0: float, s1: float, s2: float) -> Tuple[float, float]
     return rg, rl
 
 
+def _quad(fn, lo, hi):
+    """int_lo^hi fn with scipy's adaptive Gauss-Kronrod: (value, error estimate).
+    full_output keeps scipy from warning; the caller judges the estimate."""
+    val, err, *_ = integrate.quad(fn, lo, hi, limit=400, epsabs=1e-16, epsrel=1e-13, full_output=1)
+    return val, err
+
+
 def _coexistence(p: Params, weight) -> Optional[Tuple[float, float, float]]:
-    """Solve p(rho_g) = p(rho_l) = p0 and int_{rho_g}^{rho_l} (p0 - p) weight drho = 0."""
+    """Solve p(rho_g) = p(rho_l) = p0 and int_{rho_g}^{rho_l} (p0 - p) weight drho = 0.
+
+    The integral is split at the spinodal densities s1 < s2, where p has its
+    turning points, into the gas, unstable and liquid branches.  The gas
+    branch runs over rho_g .. s1 with rho_g as small as p0 allows, so it is
+    integrated in u = ln rho (drho = rho du), which spreads its decades
+    evenly; the weight of Eq. 17 grows like a power of 1/rho there.  The
+    coexistence pressure is returned only when the summed error estimate at
+    the root is below 1e-9 of the largest branch integral."""
     s1, s2 = spinodal(p)
     p_hi = float(p_eos(p, s1))
     p_lo = max(float(p_eos(p, s2)), 0.0)
     eps = 1e-13 * max(abs(p_hi), 1e-300)
 
-    def F(p0):
+    def f(p0, x):
+        return (p0 - float(p_eos(p, x))) * weight(x)
+
+    def F(p0, full=False):
         rg, rl = _roots_at(p, p0, s1, s2)
-        val, _ = integrate.quad(lambda x: (p0 - float(p_eos(p, x))) * weight(x), rg, rl,
-                                limit=400, epsabs=1e-15, epsrel=1e-13, points=[s1, s2])
+        gas = _quad(lambda u: f(p0, math.exp(u)) * math.exp(u), math.log(rg), math.log(s1))
+        mid = _quad(lambda x: f(p0, x), s1, s2)
+        liq = _quad(lambda x: f(p0, x), s2, rl)
+        val = gas[0] + mid[0] + liq[0]
+        if full:
+            return val, gas[1] + mid[1] + liq[1], max(abs(gas[0]), abs(mid[0]), abs(liq[0]))
         return val
 
     a, b = p_lo + eps, p_hi - eps
@@ -132,6 +154,9 @@ def _coexistence(p: Params, weight) -> Optional[Tuple[float, float, float]]:
     if not (fa * fb < 0):
         return None
     p0 = optimize.brentq(F, a, b, xtol=1e-18, rtol=1e-14, maxiter=500)
+    _, err, scale = F(p0, full=True)
+    if not err <= 1e-9 * scale:
+        raise ArithmeticError("coexistence integral not resolved: error estimate %.3g of %.3g" % (err, scale))
     rg, rl = _roots_at(p, p0, s1, s2)
     return rg, rl, p0
 

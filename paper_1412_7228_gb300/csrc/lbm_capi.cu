@@ -11,6 +11,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "lbm_eos_host.h"
 #include "lbm_internal.cuh"
 
 using lbm::Inst;
@@ -120,10 +121,8 @@ double eos_p(const lbm_eos& e, double rho) {
         return e.K * (rho * RT * (1.0 + n + n * n - n * n * n) / (q * q * q) - e.a * rho * rho);
     }
     if (e.kind == LBM_EOS_VDW) return e.K * (rho * RT / (1.0 - e.b * rho) - e.a * rho * rho);
-    const double m = 0.37464 + 1.54226 * e.omega - 0.26992 * e.omega * e.omega;
-    const double sq = 1.0 + m * (1.0 - std::sqrt(e.T / e.Tc));
     const double br = e.b * rho;
-    return e.K * (rho * RT / (1.0 - br) - e.a * sq * sq * rho * rho / (1.0 + 2.0 * br - br * br));
+    return e.K * (rho * RT / (1.0 - br) - e.a * lbm::pr_alpha(e) * rho * rho / (1.0 + 2.0 * br - br * br));
 }
 
 double eos_dp(const lbm_eos& e, double rho) {
@@ -137,21 +136,13 @@ double eos_dp(const lbm_eos& e, double rho) {
         const double q = 1.0 - e.b * rho;
         return e.K * (RT / (q * q) - 2.0 * e.a * rho);
     }
-    const double m = 0.37464 + 1.54226 * e.omega - 0.26992 * e.omega * e.omega;
-    const double sq = 1.0 + m * (1.0 - std::sqrt(e.T / e.Tc));
     const double br = e.b * rho, D = 1.0 + 2.0 * br - br * br, q = 1.0 - br;
-    return e.K * (RT / (q * q) - e.a * sq * sq * (2.0 * rho + 2.0 * e.b * rho * rho) / (D * D));
+    return e.K * (RT / (q * q) - e.a * lbm::pr_alpha(e) * (2.0 * rho + 2.0 * e.b * rho * rho) / (D * D));
 }
 
 double eos_rho_max(const lbm_eos& e) { return e.kind == LBM_EOS_CS ? 4.0 / e.b : 1.0 / e.b; }
 
-bool eos_valid(const lbm_eos* e) {
-    if (!e || (e->kind != LBM_EOS_CS && e->kind != LBM_EOS_VDW && e->kind != LBM_EOS_PR)) return false;
-    if (!(e->a > 0) || !(e->b > 0) || !(e->R > 0) || !(e->K > 0) || !std::isfinite(e->a + e->b + e->R + e->K))
-        return false;
-    if (e->kind == LBM_EOS_PR && !(e->Tc > 0)) return false;
-    return true;
-}
+using lbm::eos_valid;
 
 // argmin over (lo, hi) of a unimodal function, golden section
 template <class F> double golden_min(F f, double lo, double hi, double* fmin) {
@@ -449,21 +440,8 @@ int apply_schedule(lbm_ctx* c, int cfg, int sched) {
 }
 
 template <typename T> void fill_phys(lbm::Phys<T>& P, const HostParams& hp) {
-    const lbm_eos& e = hp.eos;
-    P.eos = e.kind;
+    lbm::fill_eos(P, hp.eos);
     P.flags = hp.flags;
-    P.K = T(e.K);
-    P.a = T(e.a);
-    P.b = T(e.b);
-    P.b4 = T(e.b / 4.0);
-    P.RT = T(e.R * e.T);
-    double aal = e.a;
-    if (e.kind == LBM_EOS_PR) {
-        const double m = 0.37464 + 1.54226 * e.omega - 0.26992 * e.omega * e.omega;
-        const double sq = 1.0 + m * (1.0 - std::sqrt(e.T / e.Tc));
-        aal = e.a * sq * sq;
-    }
-    P.aalpha = T(aal);
     P.A = T(hp.A);
     P.kappa = T(hp.kappa);
     P.G = T(hp.G);
@@ -558,9 +536,8 @@ int ready(lbm_ctx* c) {
 }
 
 int valid_params(const lbm_eos* eos, double A, double kappa, double G, const double* s, double rho_ref) {
-    if (!eos_valid(eos) || !s) return 0;
+    if (!lbm::eos_valid_at(eos) || !s) return 0;
     if (!std::isfinite(A) || !std::isfinite(kappa) || !std::isfinite(G) || !std::isfinite(rho_ref)) return 0;
-    if (!(eos->T > 0) || !std::isfinite(eos->T)) return 0;
     for (int k = 0; k < 9; ++k)
         if (!std::isfinite(s[k]) || s[k] <= 0.0 || s[k] >= 2.0) return 0;
     return 1;
@@ -599,7 +576,7 @@ int lbm_eos_critical(const lbm_eos* eos, double* rho_c, double* T_c, double* p_c
 }
 
 int lbm_eos_maxwell(const lbm_eos* eos, double* rho_g, double* rho_l, double* p0_out) {
-    if (!eos_valid(eos) || !(eos->T > 0)) return LBM_EINVAL;
+    if (!lbm::eos_valid_at(eos)) return LBM_EINVAL;
     const lbm_eos& e = *eos;
     const double hi = eos_rho_max(e);
     double fm;

@@ -14,14 +14,22 @@
 // until the process exits.  Host code cannot use the symbol itself as a device
 // address, so the first call on each device looks its address up with
 // cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before any stream capture begins.  All calls share the array and
-// it keeps the previous call's contents: each block writes every slot it
-// later reads, so nothing has to be cleared, but two calls whose kernels
-// overlap on the GPU (different streams or host threads) race on it.
+// first call before any stream capture begins.  Every call copies its eight
+// totals to host memory and synchronises its stream before it returns.  All
+// calls share the array and it keeps the previous call's contents: each
+// block writes every slot it later reads, so nothing has to be cleared, but
+// two calls whose kernels overlap on the GPU (different streams or host
+// threads) race on it.
+//
+// The field must be device memory of the current device: the call checks
+// this (cudaPointerGetAttributes) and rejects anything else with
+// LBM_EINVAL, as it rejects an equation of state that lbm_set_params would
+// reject, before any GPU work.
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
+#include "lbm_eos_host.h"
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -111,42 +119,50 @@ cudaError_t scratch_on_current_device(double** out) {
     return cudaSuccess;
 }
 
+// d_rho is device (or managed) memory whose device is the current one.
+bool on_current_device(const void* p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // the query's own error, not a pending one of the caller
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 }  // namespace
 }  // namespace lbm
 
 extern "C" int lbm_field_pressure_jump_static(const double* d_rho, int nx, int ny, const lbm_eos* eos, double cx,
                                               double cy, double r_in, double r_out, double* out, void* stream) {
     using namespace lbm;
-    if (!d_rho || !out || !eos || nx < 1 || ny < 1 || !(r_in >= 0) || !(r_out >= 0)) return LBM_EINVAL;
-    if (eos->kind != LBM_EOS_CS && eos->kind != LBM_EOS_VDW && eos->kind != LBM_EOS_PR) return LBM_EINVAL;
+    if (!d_rho || !out || nx < 1 || ny < 1 || !(r_in >= 0) || !(r_out >= 0)) return LBM_EINVAL;
+    if (!std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(r_in) || !std::isfinite(r_out)) return LBM_EINVAL;
+    if (!eos_valid_at(eos)) return LBM_EINVAL;   // the laws and temperatures lbm_set_params accepts
     const long long N = static_cast<long long>(nx) * ny;
     if (N > LBM_STATIC_MAX_NODES) return LBM_EINVAL;   // the static scratch holds partials for at most this many nodes
+    if (!on_current_device(d_rho)) return LBM_EINVAL;
     double* scratch = nullptr;
     if (scratch_on_current_device(&scratch) != cudaSuccess) return LBM_ECUDA;
 
     Phys<double> P;
     std::memset(&P, 0, sizeof P);
-    P.eos = eos->kind;
-    P.K = eos->K;
-    P.a = eos->a;
-    P.b = eos->b;
-    P.b4 = eos->b / 4.0;
-    P.RT = eos->R * eos->T;
-    P.aalpha = eos->a;
-    if (eos->kind == LBM_EOS_PR) {
-        const double m = 0.37464 + 1.54226 * eos->omega - 0.26992 * eos->omega * eos->omega;
-        const double sq = 1.0 + m * (1.0 - std::sqrt(eos->T / eos->Tc));
-        P.aalpha = eos->a * sq * sq;
-    }
+    fill_eos(P, *eos);
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int blocks = static_cast<int>((N + kStaticNodesPerBlock - 1) / kStaticNodesPerBlock);
+    int blocks = static_cast<int>((N + kStaticNodesPerBlock - 1) / kStaticNodesPerBlock);
     double* partials = scratch;
     double* totals = scratch + kStaticMaxBlocks * kSlots;
-    k_field_sums<<<blocks, kStaticThreads, 0, st>>>(d_rho, nx, ny, P, cx, cy, r_in, r_out, partials);
-    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
-    k_field_sums_finish<<<1, 32, 0, st>>>(partials, blocks, totals);
-    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+    // cudaLaunchKernel returns this launch's own error (never an earlier one)
+    void* a1[] = {&d_rho, &nx, &ny, &P, &cx, &cy, &r_in, &r_out, &partials};
+    if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_field_sums), dim3(blocks), dim3(kStaticThreads), a1, 0, st) !=
+        cudaSuccess)
+        return LBM_ECUDA;
+    void* a2[] = {&partials, &blocks, &totals};
+    if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_field_sums_finish), dim3(1), dim3(32), a2, 0, st) !=
+        cudaSuccess)
+        return LBM_ECUDA;
     double s[kSlots];
     if (cudaMemcpyAsync(s, totals, sizeof s, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LBM_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return LBM_ECUDA;

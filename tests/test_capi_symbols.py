@@ -67,3 +67,23 @@ def test_product_eos_helpers_agree_with_the_oracle():
         assert abs(P.lbm_eos_pressure(e, rho) - ref) < 1e-15
     s, c, r2 = P.lbm_laplace_fit([0.3, 0.2, 0.15], [10.0, 15.0, 20.0])
     assert abs(s - 3.0) < 1e-12 and abs(c) < 1e-12 and abs(r2 - 1) < 1e-12
+
+
+@pytest.mark.parametrize("bad", [dict(T=0.0), dict(T=-0.07), dict(T=float("nan")), dict(a=0.0), dict(b=-4.0),
+                                 dict(R=0.0), dict(K=0.0), dict(kind=7), dict(kind=3, Tc=0.0)])
+def test_static_sampling_rejects_what_set_params_rejects(liblbm, bad):
+    """lbm_field_pressure_jump_static refuses an equation of state or a
+    temperature that lbm_set_params refuses, before it touches the GPU
+    (the pointer is never dereferenced: no GPU is needed here)."""
+    import numpy as np
+    import paper_1412_7228_gb300 as P
+    kw = dict(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, T=0.07, omega=0.344, Tc=0.1)
+    kw.update(bad)
+    eos = P.Eos(**kw)
+    out = np.zeros(8)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = P.lib().lbm_field_pressure_jump_static(ctypes.c_void_p(1 << 20), 64, 64, ctypes.byref(eos.c()), 32.0, 32.0,
+                                                8.0, 20.0, out.ctypes.data_as(dp), None)
+    assert rc == P.lbm.LBM_EINVAL
+    assert P.lib().lbm_eos_maxwell(ctypes.byref(eos.c()), out.ctypes.data_as(dp), out.ctypes.data_as(dp),
+                                   out.ctypes.data_as(dp)) == P.lbm.LBM_EINVAL
