@@ -118,25 +118,51 @@ def kernel_traffic(prec_name, kernel):
         return None
 
 
-def fp64_alu_roofline(mlups, kernel):
-    """FP64 step against the FP64 pipe: GB300 issues 2 FP64 thread-operations
-    per clock per SM; the kernel's FP64 operations per lattice update come
-    from the committed ncu summary (valid for the kernel it names, while the
-    kernel sources are unchanged)."""
-    sha = kernel_sources_sha()
+def oracle_flops_per_update(law="carnahan_starling"):
+    """Floating-point operations of one time step per lattice node of the
+    FP64 oracle (its traced build, common subexpressions counted once: the
+    method's arithmetic, without the kernel's own refinement steps), as
+    committed by tests/golden/make_op_count.py."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_op_count.json")) as fh:
+            return float(json.load(fh)["counts"][law]["flops_per_update"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def fp64_pipe_profile(kernel):
+    """ncu figures of the FP64 step kernel (FP64 pipe utilisation and
+    executed FP64 instructions per update), valid only for the kernel the
+    committed summary names and while the kernel sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "step_fp64_1024_alu.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
-        if kv.get("kernel_sources_sha256_16") != sha or kv.get("kernel") != kernel:
-            return None
-        ops = float(kv["fp64_ops_per_update"])
-    except (OSError, KeyError, ValueError):
+    except OSError:
         return None
-    sm_mhz, sms = 2070.0, 152
-    peak = 2.0 * sms * sm_mhz * 1e6 / 1e9          # G FP64 thread-operations per second
+    if kv.get("kernel_sources_sha256_16") != kernel_sources_sha() or kv.get("kernel") != kernel:
+        return None
+    out = {}
+    for k in ("fp64_pipe_active", "fp64_inst_per_update"):
+        try:
+            out[k] = float(kv[k])
+        except (KeyError, ValueError):
+            pass
+    return out or None
+
+
+def fp64_roofline(mlups, flops_per_s_peak):
+    """FP64 step against the measured FP64 peak: the oracle's operations per
+    update times the update rate, over the FMA-chain rate of this GPU
+    measured in the same run (lbm_fp64_fma_rate)."""
+    ops = oracle_flops_per_update()
+    if ops is None or not flops_per_s_peak:
+        return None
     achieved = ops * mlups * 1e6 / 1e9
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP64 ops/s", "frac": achieved / peak,
-            "ops_per_update": ops, "peak_from": "2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz"}
+    peak = flops_per_s_peak / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+            "peak_kind": "measured", "flops_per_update": ops,
+            "flops_from": "oracle operation count per update (tests/golden/oracle_op_count.json)",
+            "peak_from": "FP64 FMA chains on every SM, this run (lbm_fp64_fma_rate)"}
 
 
 class ClockSampler:
@@ -222,6 +248,63 @@ def time_steps(torch, lat, steps):
     e1.record(st)
     e1.synchronize()
     return e0.elapsed_time(e1) / 1000.0
+
+
+def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
+    """The batched uneven sweep workload (64 static droplets, L uniform over
+    {128, 256, 512, 1024}, R0 = 0.2 L, T/Tc ~ U[0.6, 0.85], kappa ~ U[0, 0.6],
+    A ~ U[-0.9, -0.8], FP32) stepped `steps` times, once as one batched
+    context (one launch per step, tile and CTA schedule autotuned) and once as
+    64 one-lattice contexts stepped one after another on one stream (each
+    with its own autotuned tile), both from CUDA graphs and both timed with
+    CUDA events on their stream.  The results of the two must be the same
+    bits (compared through each drop's Laplace sampling)."""
+    from paper_1412_7228_gb300 import sweep as SW
+    drops = SW.sweep_droplets(n, seed)
+    nodes = sum(d.L * d.L for d in drops)
+    st = torch.cuda.Stream()
+    b = P.Batch([d.L for d in drops], [d.L for d in drops], P.LBM_FP32, stream=st)
+    for i, d in enumerate(drops):
+        SW._setup(b, i, d)
+    tile, sched, _ = b.autotune(5)
+    b.use_graphs(True)
+    b.step(64)
+    b.sync()
+    t_b = time_steps(torch, b, steps)
+    b.sync()
+    launches_per_step = (b.kernel_launches) / max(b.steps_done, 1)
+    res_b = [b.measure(i, d.L / 2, d.L / 2, d.radius / 2, d.radius + SW.R_OUT_GAP)["dp"] for i, d in enumerate(drops)]
+    b.close()
+
+    lats = []
+    for d in drops:
+        lat = P.Lattice(d.L, d.L, P.LBM_FP32, stream=st)
+        SW._setup(lat, 0, d)
+        lat.autotune(5)
+        lat.use_graphs(True)
+        lat.step(64)
+        lats.append(lat)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for lat in lats:
+        lat.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    t_s = e0.elapsed_time(e1) / 1000.0
+    res_s = []
+    for lat, d in zip(lats, drops):
+        lat.sync()
+        res_s.append(lat.measure(0, d.L / 2, d.L / 2, d.radius / 2, d.radius + SW.R_OUT_GAP)["dp"])
+        lat.close()
+    same = all(x == y for x, y in zip(res_b, res_s))
+    return {"workload": "%d static droplets, L in {128, 256, 512, 1024}, R0 = 0.2 L, seed %d, FP32, %d steps "
+                        "(the configured 20000 steps cut to keep the benchmark short)" % (n, seed, steps),
+            "nodes": nodes, "steps": steps, "batched_s": t_b, "sequential_s": t_s, "speedup": t_s / t_b,
+            "batched_mlups": nodes * steps / t_b / 1e6, "sequential_mlups": nodes * steps / t_s / 1e6,
+            "batched_tile": [tile, sched], "batched_launches_per_step": launches_per_step,
+            "results_bit_identical": same, "timing": "CUDA events on the shared stream, graphs on both arms"}
 
 
 def cpu_model(cpuinfo="/proc/cpuinfo"):
@@ -369,15 +452,21 @@ def run_ours(args):
         lat64.step(min(args.warmup, 10))
         lat64.sync()
         k64 = max(32, args.steps // 32)
-        t64 = time_steps(torch, lat64, k64)
-        lat64.sync()
+        with ClockSampler(local) as clk64:
+            t64 = time_steps(torch, lat64, k64)
+            lat64.sync()
+            fma_flops, fma_s = P.lbm.lbm_fp64_fma_rate(4096, lat64.stream.cuda_stream)
         m64 = N * k64 / t64 / 1e6
         fp64 = {"value": m64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1000.0,
                 "hbm_frac": 144 * N / (t64 / k64) / 1e9 / peak, "bytes_per_update": 144,
-                "kernel": "lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(P.lbm_tile_configs(P.LBM_FP64)[TILE_FP64])}
-        alu = fp64_alu_roofline(m64, fp64["kernel"])
-        if alu:
-            fp64["roofline"] = alu
+                "kernel": "lbm::k_step<double,%d,%d,%d,%d,1>" % tuple(P.lbm_tile_configs(P.LBM_FP64)[TILE_FP64]),
+                "fp64_peak_gflops": fma_flops / 1e9, "fp64_peak_launch_ms": fma_s * 1e3, "clocks": clk64.summary()}
+        roof64 = fp64_roofline(m64, fma_flops)
+        if roof64:
+            fp64["roofline"] = roof64
+        prof64 = fp64_pipe_profile(fp64["kernel"])
+        if prof64:
+            fp64["ncu"] = prof64
         lat64.close()
 
     # ---- the same step on the paper's other synthetic workloads -----------
@@ -437,6 +526,11 @@ def run_ours(args):
                "h2d_bytes_per_step": 8 * N / args.steps, "d2h_bytes_per_step": 8 * N / args.steps,
                "what": "lbm_init_density from pinned host rho, lbm_step(K), lbm_read_fields(rho) to host"}
 
+    # ---- batched uneven sweep against the same lattices one after another ---
+    batched = None
+    if not args.no_sweep:
+        batched = batched_vs_sequential(torch, P, args.sweep_steps)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cn = args.cpu_n
@@ -455,7 +549,8 @@ def run_ours(args):
             "config": workload_config(nx, ny, args.precision, dict(
                 {"tile": list(tile), "parallelism": "replicas" if ws > 1 else "single"}, **graph_use(args.steps))),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": launches, "fp64": fp64, "other_workloads": others, "status_ok": status_ok,
+            "gpu_launches": launches, "fp64": fp64, "other_workloads": others, "batched_sweep": batched,
+            "status_ok": status_ok,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -481,6 +576,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-workloads", action="store_true", help="skip the droplet and flat-interface timings")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched-vs-sequential droplet sweep")
+    ap.add_argument("--sweep-steps", type=int, default=2000)
     ap.add_argument("--cpu-n", type=int, default=2048)
     ap.add_argument("--cpu-steps", type=int, default=8)
     args = ap.parse_args()

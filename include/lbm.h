@@ -104,6 +104,16 @@ int lbm_laplace_fit(int n, const double* dp, const double* R, double* sigma, dou
  * error. */
 int lbm_fp64_math_check(double lo, double hi, long long n, unsigned long long result[4]);
 
+/* Measured FP64 peak of the current device, the denominator of the FP64
+ * step's roofline (the paper has no counterpart: it is a measurement aid).
+ * Every resident thread of every SM runs 8 independent chains of `iters`
+ * fused multiply-adds on `stream` (NULL: legacy default stream); one warm-up
+ * launch, then the fastest of three launches timed with CUDA events.
+ * flops_per_s = 2 x FMAs / seconds (an FMA is two floating-point operations);
+ * seconds = that launch's duration.  Synchronous.  LBM_EINVAL unless
+ * iters >= 1 and both outputs are given; LBM_ECUDA on a device error. */
+int lbm_fp64_fma_rate(int iters, void* stream, double* flops_per_s, double* seconds);
+
 /* ---- Context ------------------------------------------------------------ */
 
 /* Bytes of device memory one context of these lattices needs when the caller

@@ -211,3 +211,16 @@ def macro(p: Params, f: np.ndarray):
     if rc < 0:
         raise RuntimeError("orc_macro failed")
     return tuple(outs)
+
+
+def op_count(*args) -> dict:
+    """Floating-point operations of one oracle time step per lattice node,
+    from the traced build of the oracle (op_count.cpp): op_count(eos, nx, ny)
+    -> {flops_per_update, add_sub_per_update, mul_per_update, div_per_update,
+    sqrt_per_update}; op_count("meq") or op_count("source_s") -> {flops} of
+    that piece alone."""
+    import subprocess
+    _build.build()
+    out = subprocess.run([_build.OPC_BIN] + [str(a) for a in args], check=True, capture_output=True,
+                         text=True).stdout
+    return {k: float(v) for k, v in (line.split("=", 1) for line in out.split())}

@@ -1,4 +1,5 @@
-"""Compile the FP64 CPU oracle (test infrastructure) into oracle/liboracle.so.
+"""Compile the FP64 CPU oracle (test infrastructure) into oracle/liboracle.so,
+and its operation counter into oracle/op_count.
 
 Plain gcc, no shared headers with the CUDA path.  ``-ffp-contract=off`` keeps
 the rounding identical on x86_64 and aarch64 hosts.
@@ -9,17 +10,27 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lbm_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
+OPC_SRC = os.path.join(HERE, "op_count.cpp")
+OPC_BIN = os.path.join(HERE, "op_count")
+
+
+def _stale(out: str, *srcs: str) -> bool:
+    return not os.path.exists(out) or any(os.path.getmtime(out) < os.path.getmtime(s) for s in srcs)
 
 
 def build(force: bool = False) -> str:
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    """liboracle.so, and the operation counter op_count (lbm_oracle.c traced
+    in C++, see op_count.cpp)."""
+    if force or _stale(LIB, SRC):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+    if force or _stale(OPC_BIN, SRC, OPC_SRC):
+        tmp = OPC_BIN + ".tmp%d" % os.getpid()
+        subprocess.run(["g++", "-O1", "-std=c++17", "-Wall", "-o", tmp, OPC_SRC], check=True)
+        os.replace(tmp, OPC_BIN)
     return LIB
 
 

@@ -286,7 +286,62 @@ __global__ void k_math_check(long long n, double lo, double hi, unsigned long lo
     }
 }
 
+// FP64 fused multiply-add throughput: every thread runs kFmaChains
+// independent chains x <- x m + c (m < 1, so x stays finite) for `iters`
+// iterations.  The chains' sum is compared with a value it cannot take, so
+// the compiler keeps every FMA; nothing is stored.
+constexpr int kFmaChains = 8;
+constexpr int kFmaThreads = 256;
+__device__ double g_fma_sink;
+__global__ void __launch_bounds__(kFmaThreads) k_fp64_fma(int iters, double m, double c) {
+    double x[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) x[k] = 1e-3 * threadIdx.x + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kFmaChains; ++k) x[k] = fma(x[k], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) s += x[k];
+    if (s == -1.0) g_fma_sink = s;
+}
+
 }  // namespace
+
+cudaError_t aux_fp64_fma_rate(int iters, cudaStream_t st, double* flops_per_s, double* seconds) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * (2048 / kFmaThreads);   // every SM full
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    float best = 0.0f;
+    for (int r = 0; r < 4 && e == cudaSuccess; ++r) {   // the first launch warms up
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) {
+            k_fp64_fma<<<blocks, kFmaThreads, 0, st>>>(iters, 0.999, 1e-3);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && r > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * blocks * kFmaThreads * static_cast<double>(kFmaChains) * iters;
+    *seconds = best * 1e-3;
+    *flops_per_s = flops / (*seconds);
+    return cudaSuccess;
+}
 
 cudaError_t aux_init(const Inst& h, const Inst* d, const double* rho, const double* ux, const double* uy,
                      int parity, cudaStream_t st) {

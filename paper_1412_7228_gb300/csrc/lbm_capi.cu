@@ -631,6 +631,15 @@ int lbm_fp64_math_check(double lo, double hi, long long n, unsigned long long re
     return rc;
 }
 
+int lbm_fp64_fma_rate(int iters, void* stream, double* flops_per_s, double* seconds) {
+    if (iters < 1 || !flops_per_s || !seconds) return LBM_EINVAL;
+    if (lbm::aux_fp64_fma_rate(iters, static_cast<cudaStream_t>(stream), flops_per_s, seconds) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ECUDA;
+    }
+    return LBM_OK;
+}
+
 int lbm_laplace_fit(int n, const double* dp, const double* R, double* sigma, double* icpt, double* r2) {
     if (n < 2 || !dp || !R) return LBM_EINVAL;
     double sx = 0, sy = 0, sxx = 0, sxy = 0;

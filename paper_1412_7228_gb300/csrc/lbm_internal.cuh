@@ -296,6 +296,8 @@ cudaError_t aux_field(const Inst& host, const Inst* d_inst, int parity, int fiel
                       cudaStream_t st);
 // out: 4 device words (see lbm_fp64_math_check); default stream.
 cudaError_t aux_math_check(long long n, double lo, double hi, unsigned long long* out);
+// FP64 FMA throughput of the current device (see lbm_fp64_fma_rate).
+cudaError_t aux_fp64_fma_rate(int iters, cudaStream_t st, double* flops_per_s, double* seconds);
 constexpr int kReduceBlocks = 304;   // 2 CTAs per SM of a 152-SM GB300: partial sums of FP64 reductions
 constexpr int kReduceSlots = 8;
 cudaError_t aux_measure(const Inst& host, const Inst* d_inst, int parity, double cx, double cy,

@@ -30,6 +30,7 @@ _CODES = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA", LBM_EU
 
 EXPORTS = [
     "lbm_eos_pressure", "lbm_eos_critical", "lbm_eos_maxwell", "lbm_laplace_fit", "lbm_fp64_math_check",
+    "lbm_fp64_fma_rate",
     "lbm_required_bytes", "lbm_batch_required_bytes", "lbm_create", "lbm_batch_create", "lbm_destroy",
     "lbm_set_params", "lbm_batch_set_params", "lbm_set_viscosity", "lbm_batch_set_viscosity",
     "lbm_init_density", "lbm_batch_init_density",
@@ -93,6 +94,7 @@ def lib():
         "lbm_fp64_math_check": ([ctypes.c_double, ctypes.c_double, ctypes.c_longlong,
                                  ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
         "lbm_eos_maxwell": ([E, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_fp64_fma_rate": ([ctypes.c_int, _vp, _dp, _dp], ctypes.c_int),
         "lbm_laplace_fit": ([ctypes.c_int, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
         "lbm_required_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
         "lbm_batch_required_bytes": ([ctypes.c_int, _ip, _ip, ctypes.c_int], ctypes.c_size_t),
@@ -216,6 +218,14 @@ def lbm_fp64_math_check(lo: float, hi: float, n: int) -> dict:
     r = (ctypes.c_ulonglong * 4)()
     _check(None, lib().lbm_fp64_math_check(lo, hi, n, r))
     return {"rcp_ulp": int(r[0]), "div_ulp": int(r[1]), "sqrt_ulp": int(r[2]), "sqrt_special_ok": bool(r[3])}
+
+
+def lbm_fp64_fma_rate(iters: int = 4096, stream_ptr: int = 0):
+    """Measured FP64 throughput of the current device: (FLOP/s, seconds of
+    the timed launch); an FMA counts as two floating-point operations."""
+    f, t = ctypes.c_double(), ctypes.c_double()
+    _check(None, lib().lbm_fp64_fma_rate(int(iters), ctypes.c_void_p(stream_ptr), ctypes.byref(f), ctypes.byref(t)))
+    return f.value, t.value
 
 
 LBM_STATIC_MAX_NODES = 16777216

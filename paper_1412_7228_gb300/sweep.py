@@ -15,6 +15,7 @@ least-squares fit runs in liblbm.so.  Two drivers:
 Run as ``python -m paper_1412_7228_gb300.sweep --help``.
 """
 import argparse
+import functools
 import json
 import math
 import time
@@ -31,13 +32,19 @@ S_DEFAULT = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
 CS = dict(kind=L.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
 
 
-def cs_eos(t_over_tc: float) -> Tuple[L.Eos, float, float]:
-    """Carnahan-Starling law at T = t_over_tc * Tc and its Maxwell densities."""
+@functools.lru_cache(maxsize=None)
+def _cs_state(t_over_tc: float) -> Tuple[float, float, float]:
     eos = L.Eos(**CS)
     _, Tc, _ = L.lbm_eos_critical(eos)
     eos.T = t_over_tc * Tc
     rg, rl, _ = L.lbm_eos_maxwell(eos)
-    return eos, rg, rl
+    return eos.T, rg, rl
+
+
+def cs_eos(t_over_tc: float) -> Tuple[L.Eos, float, float]:
+    """Carnahan-Starling law at T = t_over_tc * Tc and its Maxwell densities."""
+    T, rg, rl = _cs_state(float(t_over_tc))
+    return L.Eos(T=T, **CS), rg, rl
 
 
 @dataclass
@@ -54,6 +61,8 @@ class Droplet:
     rho_g: float = float("nan")
     umax: float = float("nan")
     status: int = 0
+    R_drift: float = float("nan")   # relative change of R_eq over the sampling window
+    n_samples: int = 0
 
     @property
     def sigma_single(self) -> float:
@@ -67,19 +76,41 @@ def _setup(batch: L.Batch, i: int, d: Droplet, s=S_DEFAULT):
     L.Batch.init_density(batch, i, I.droplet_density(d.L, d.L, d.radius, rl, rg))
 
 
-def _harvest(batch: L.Batch, i: int, d: Droplet, r_out_gap: float = 10.0):
+R_OUT_GAP = 10.0   # p_out is sampled at r >= R0 + 10 (the gas beyond the interface)
+# Laplace sampling window: the mean of Delta p (and of R_eq and the phase
+# densities) over the last WINDOW_STEPS steps, sampled every WINDOW_EVERY.
+# A static drop keeps acoustic standing waves in the gas between it and its
+# periodic images (periods of 60-270 steps at 256^2, decaying over ~10^4
+# steps); one instant's Delta p carries them (up to 3 % of Delta p for
+# R0 = 60 at 3e4 steps), the window mean leaves the Laplace pressure.
+WINDOW_STEPS, WINDOW_EVERY = 2000, 20
+
+
+def _sample(batch: L.Batch, i: int, d: Droplet) -> Dict:
+    return batch.measure(i, d.L / 2.0, d.L / 2.0, d.radius / 2.0, d.radius + R_OUT_GAP)
+
+
+def _harvest(batch: L.Batch, i: int, d: Droplet, acc: Optional[List[Dict]] = None):
+    """Results of droplet i: the window means of acc (its samples) when
+    given, else one sample now."""
     d.status = batch.status(i)
     if d.status != L.LBM_OK:
         return
-    m = batch.measure(i, d.L / 2.0, d.L / 2.0, d.radius / 2.0, d.radius + r_out_gap)
-    d.dp, d.R_eq, d.rho_l, d.rho_g = m["dp"], m["R_eq"], m["rho_in"], m["rho_out"]
+    samples = acc if acc else [_sample(batch, i, d)]
+    mean = lambda k: float(np.mean([m[k] for m in samples]))
+    d.dp, d.R_eq, d.rho_l, d.rho_g = mean("dp"), mean("R_eq"), mean("rho_in"), mean("rho_out")
+    d.R_drift = (samples[-1]["R_eq"] - samples[0]["R_eq"]) / max(abs(samples[-1]["R_eq"]), 1e-300)
+    d.n_samples = len(samples)
     d.umax = batch.stats(i)["umax"]
 
 
 def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP32, autotune: bool = True,
-              graphs: bool = True, s=S_DEFAULT, schedule: Optional[Tuple[int, int]] = None) -> Dict:
+              graphs: bool = True, s=S_DEFAULT, schedule: Optional[Tuple[int, int]] = None,
+              window: Optional[Tuple[int, int]] = None) -> Dict:
     """Step every droplet together; fill in the per-droplet results.
-    schedule: (tile configuration, CTA schedule) instead of autotuning."""
+    schedule: (tile configuration, CTA schedule) instead of autotuning.
+    window: (span, every): Laplace sampling averaged over the last `span`
+    steps, one sample every `every` steps (None: one sample at the end)."""
     import torch
     batch = L.Batch([d.L for d in droplets], [d.L for d in droplets], precision)
     for i, d in enumerate(droplets):
@@ -91,18 +122,33 @@ def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP
         tune = batch.autotune(5)
     if graphs:
         batch.use_graphs(True)
+    acc = None
+    span, every = window if window else (0, 1)
+    if span >= steps or span % every:
+        raise ValueError("the window must be a whole number of sampling intervals shorter than the run")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    batch.step(steps)
+    sample_s = 0.0
+    batch.step(steps - span)
+    if window:
+        acc = [[] for _ in droplets]
+        for k in range(span // every + 1):
+            if k:
+                batch.step(every)
+            t1 = time.perf_counter()
+            for i, d in enumerate(droplets):
+                acc[i].append(_sample(batch, i, d))
+            sample_s += time.perf_counter() - t1
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    dt = time.perf_counter() - t0 - sample_s
     launches = batch.kernel_launches
     for i, d in enumerate(droplets):
-        _harvest(batch, i, d)
+        _harvest(batch, i, d, acc[i] if acc else None)
     batch.clear_status()
     batch.close()
     nodes = sum(d.L * d.L for d in droplets)
-    return {"seconds": dt, "mlups": nodes * steps / dt / 1e6, "tune": tune, "launches": launches}
+    return {"seconds": dt, "mlups": nodes * steps / dt / 1e6, "tune": tune, "launches": launches,
+            "sampling_seconds": sample_s}
 
 
 def run_sequential(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP32, graphs: bool = True,
@@ -139,19 +185,31 @@ class LaplaceFit:
     radii: List[float] = field(default_factory=list)
 
 
+def in_equilibrium(d: Droplet, max_drift: float = 1e-3) -> bool:
+    """Laplace's law holds for drops at equilibrium: a drop is used when it
+    is stable, still a liquid drop (its core denser than the gas around it
+    by half the Maxwell density gap) and, when sampled over a window, its
+    equimolar radius moved by less than max_drift there (an evaporating drop
+    keeps shrinking)."""
+    if d.status != L.LBM_OK or not (np.isfinite(d.dp) and np.isfinite(d.R_eq) and d.R_eq > 0):
+        return False
+    _, rg, rl = cs_eos(d.t_over_tc)
+    if not d.rho_l - d.rho_g >= 0.5 * (rl - rg):
+        return False
+    return d.n_samples <= 1 or abs(d.R_drift) <= max_drift
+
+
 def laplace_sweep(radii=(20, 30, 40, 50, 60), kappas=(0.0, 0.1, 0.3, 0.5), t_over_tc=(0.6, 0.7, 0.8), L_=256,
-                  steps=30000, A=-0.85, precision=L.LBM_FP32, autotune=True) -> Tuple[List[LaplaceFit], Dict]:
+                  steps=30000, A=-0.85, precision=L.LBM_FP32, autotune=True,
+                  window=(WINDOW_STEPS, WINDOW_EVERY)) -> Tuple[List[LaplaceFit], Dict]:
     drops = [Droplet(L_, float(R), tr, A, k) for tr in t_over_tc for k in kappas for R in radii]
-    info = run_batch(drops, steps, precision, autotune=autotune)
+    info = run_batch(drops, steps, precision, autotune=autotune, window=window)
     info["droplets"] = [{k: getattr(d, k) for k in ("radius", "t_over_tc", "kappa", "dp", "R_eq", "rho_l", "rho_g",
-                                                     "umax", "status")} for d in drops]
+                                                     "umax", "status", "R_drift")} for d in drops]
     fits = []
     for tr in t_over_tc:
         for k in kappas:
-            # Laplace's law holds for drops at equilibrium: one that lost more than a
-            # quarter of its radius to the gas (evaporating) is left out of the fit
-            grp = [d for d in drops if d.t_over_tc == tr and d.kappa == k and d.status == L.LBM_OK
-                   and np.isfinite(d.dp) and np.isfinite(d.R_eq) and d.R_eq >= 0.75 * d.radius]
+            grp = [d for d in drops if d.t_over_tc == tr and d.kappa == k and in_equilibrium(d)]
             if len(grp) < 2:
                 continue
             sigma, icpt, r2 = L.lbm_laplace_fit([d.dp for d in grp], [d.R_eq for d in grp])

@@ -84,16 +84,21 @@ def test_traffic_figure_is_used_only_for_the_profiled_kernel():
 
 
 def test_fp64_roofline_and_cpu_model_records(tmp_path):
-    """The FP64 ALU roofline uses the committed operation count only for the
-    kernel it names; the CPU model is read from x86 and Arm cpuinfo alike."""
+    """The FP64 roofline divides the oracle's operation count per update
+    times the update rate by the measured FP64 peak; the ncu figures of the
+    FP64 kernel are used only for the kernel they name; the CPU model is
+    read from x86 and Arm cpuinfo alike."""
     sys.path.insert(0, ROOT)
+    import json
     import bench
-    path = os.path.join(ROOT, "profiles", "step_fp64_1024_alu.txt")
-    kv = dict(l.strip().split("=", 1) for l in open(path) if "=" in l and not l.startswith("#"))
-    r = bench.fp64_alu_roofline(2000.0, kv["kernel"])
-    if r is not None:
-        assert r["bound"] == "alu" and abs(r["frac"] - 2000.0e6 * float(kv["fp64_ops_per_update"]) / 1e9 / r["peak"]) < 1e-12
-    assert bench.fp64_alu_roofline(2000.0, "lbm::another_kernel") is None
+    ops = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_op_count.json")))
+    ops = ops["counts"]["carnahan_starling"]["flops_per_update"]
+    assert bench.oracle_flops_per_update() == ops
+    r = bench.fp64_roofline(2000.0, 1.25e12)
+    assert r["bound"] == "alu" and r["peak_kind"] == "measured" and r["unit"] == "GFLOP/s"
+    assert abs(r["achieved"] - ops * 2000.0e6 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / 1250.0) < 1e-12
+    assert bench.fp64_roofline(2000.0, None) is None
+    assert bench.fp64_pipe_profile("lbm::another_kernel") is None
     x86 = tmp_path / "x86"
     x86.write_text("processor\t: 0\nmodel name\t: Some CPU @ 2.0GHz\n")
     arm = tmp_path / "arm"
