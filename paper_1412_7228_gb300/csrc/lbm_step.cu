@@ -96,7 +96,9 @@ template <typename T> using Regs = typename RegsSel<T>::type;
 // f: pre-collision f_a - t_a rho_ref; out: post-collision, same form.
 // P: the relaxation constants (register copies for FP32, references into the
 // descriptor for FP64).
-template <typename T, typename RP>
+// VISC = false: the tile's lattice has fixed shear rates (no per-node
+// viscosity law), decided once per tile by the caller.
+template <typename T, bool VISC, typename RP>
 __device__ __forceinline__ void collide(const RP& P, const T (&f)[9], T Fx, T Fy, T Qxx, T Qyy, T Qxy,
                                         T (&out)[9]) {
     const T Sa = (f[1] + f[3]) + (f[2] + f[4]);
@@ -135,7 +137,7 @@ __device__ __forceinline__ void collide(const RP& P, const T (&f)[9], T Fx, T Fy
     const T ms6 = fma(T(P.nhs6), Fy, fma(T(P.ns6), m6 + ruy, m6));
     // shear rates: fixed, or from the density-dependent viscosity (Section 4.2)
     T ns7 = T(P.ns7), ns8 = T(P.ns8), h2s7 = T(P.h2s7), hs8 = T(P.hs8);   // h2s7 = 2 hs7
-    if (P.var_visc) {
+    if (VISC && P.var_visc) {
         const T w = fmin(fmax((rho - T(P.visc_rho_g)) * T(P.visc_inv_drho), T(0)), T(1));
         const T sn = Fast<T>::rcp(fma(T(3), fma(w, T(P.dnu), T(P.nu_g)), T(0.5)));
         ns7 = ns8 = -sn;
@@ -186,13 +188,15 @@ template <> struct EosSel<float> { using type = EosOf<float, float>; };
 template <typename T> using EosRegs = typename EosSel<T>::type;
 
 // Eq. 10 radicand with the pressure laws of lbm_internal.cuh, using Fast<T>.
-template <typename T> __device__ __forceinline__ T radicand_step(const EosRegs<T>& P, T rho) {
+// EOSK = LBM_EOS_* fixes the law at compile time; 0 reads it from the constants.
+template <int EOSK, typename T> __device__ __forceinline__ T radicand_step(const EosRegs<T>& P, T rho) {
+    const int eos = EOSK ? EOSK : P.eos;
     T p;
-    if (P.eos == LBM_EOS_CS) {
+    if (eos == LBM_EOS_CS) {
         const T n = P.b4 * rho, q = T(1) - n;
         const T num = fma(n, fma(n, T(1) - n, T(1)), T(1));
         p = P.K * fma(-P.a * rho, rho, Fast<T>::div(rho * P.RT * num, q * q * q));
-    } else if (P.eos == LBM_EOS_VDW) {
+    } else if (eos == LBM_EOS_VDW) {
         p = P.K * fma(-P.a * rho, rho, Fast<T>::div(rho * P.RT, fma(-P.b, rho, T(1))));
     } else {
         const T br = P.b * rho;
@@ -246,6 +250,161 @@ __device__ __forceinline__ const Phys<double>& phys_of(const BatchArgs<double>&,
     return phys<double>(I);
 }
 
+// rho and psi (Eq. 10) of the tile and its 1-node ring, into sp.  A density
+// outside the EOS's psi domain gives a negative radicand and a NaN psi
+// (square root), which reaches every output of the owned node (F and Q are
+// linear in psi, 0 x NaN is NaN): the collision's NaN check records it.
+// Ring nodes beyond the lattice's ghost images feed no owned node.
+template <typename Gm, int EOSK, typename T>
+__device__ __forceinline__ void psi_ring(const T* sf, T* sp, const EosRegs<T>& E, T rho_ref, int tid, int tx,
+                                         int ty) {
+    constexpr int BX = Gm::BX;
+    auto ring = [&](int i, int j) {
+        const T* q = sf + (j + 1) * Gm::WB + (i + Gm::HX - 1);
+        T g[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) g[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
+        sp[j * Gm::WP + i] = Fast<T>::sqrt(radicand_step<EOSK>(E, rho_ref + rho_dev(g)));
+    };
+    // rows ty, ty + TY, ... (unrolled where a thread owns several rows; the
+    // one-row shapes run under a tighter register bound); the two right-hand
+    // ring columns go to the threads the last row pass leaves idle when there
+    // are enough, so that no warp evaluates more ring nodes than the busiest
+    // row pass gives it
+    constexpr int K = (Gm::HP + Gm::TY - 1) / Gm::TY;
+    constexpr bool kMerge = Gm::ROWS > 1 && (K * Gm::TY - Gm::HP) * BX >= 2 * Gm::HP;
+    if constexpr (Gm::ROWS > 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = ty + k * Gm::TY;
+            if (j < Gm::HP) {
+                ring(tx, j);
+            } else if (kMerge && k == K - 1) {
+                const int e = (j - Gm::HP) * BX + tx;
+                if (e < 2 * Gm::HP) ring(BX + (e & 1), e >> 1);
+            }
+        }
+    } else {
+        for (int j = ty; j < Gm::HP; j += Gm::TY) ring(tx, j);
+    }
+    if (!kMerge)
+        for (int e = tid; e < 2 * Gm::HP; e += Gm::NT) ring(BX + (e & 1), e >> 1);
+}
+
+// Force, modifying tensor, collision and store of the thread's ROWS nodes
+// (consecutive rows of column tx).  Returns true when a node's results are
+// NaN.  FAST: every node of the tile lies inside the lattice and away from
+// its two border rows and columns (no bounds checks, no ghost images), G != 0
+// and the shear rates are fixed; decided once per tile.
+template <typename Gm, bool FAST, typename T, typename RP>
+__device__ __forceinline__ bool collide_rows(const T* sf, const T* sp, const Phys<T>& P, const RP& R, T* __restrict__ dst,
+                                             long long plane, int pitch, int x0, int y0, int nx, int ny, bool border,
+                                             bool interact_rt, int tx, int ty) {
+    const bool interact = FAST || interact_rt;
+    // periodic images in the ghost cells read by the neighbouring tiles
+    auto ghost = [&](T* o, int x, int y, const T (&v)[9]) {
+        const bool xl = x < 2, xr = x >= nx - 2, yl = y < 2, yr = y >= ny - 2;
+        if (!(xl || xr || yl || yr)) return;
+        const int oxs[3] = {0, xl ? nx : 0, xr ? -nx : 0};
+        const int oys[3] = {0, yl ? ny : 0, yr ? -ny : 0};
+        const bool hx[3] = {true, xl, xr};
+        const bool hy[3] = {true, yl, yr};
+        for (int iy = 0; iy < 3; ++iy)
+            for (int ix = 0; ix < 3; ++ix) {
+                if (!(hx[ix] && hy[iy]) || (ix == 0 && iy == 0)) continue;
+                T* g = o + static_cast<long long>(oys[iy]) * pitch + oxs[ix];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) g[a * plane] = v[a];
+            }
+    };
+
+    // each thread owns ROWS consecutive rows of one column; the 3x3 psi
+    // neighbourhood slides down with it (three new loads per node)
+    const T G = P.G, A = P.A;
+    const T negGw = -G * T(1.0 / 12.0), hA = T(0.5) * A, omA = T(1) - A;
+    const T kGw = P.kappa * G * T(1.0 / 24.0);
+    const int ly0 = ty * Gm::ROWS;
+    const T* s0 = sp + (ly0 + 1) * Gm::WP + (tx + 1);   // psi of node (tx, ly0)
+    // FP64 slides the squares of the window too (six FP64 products fewer
+    // per node); FP32 forms them per node, which keeps it to fewer
+    // registers and measured faster
+    constexpr bool kSlideSquares = sizeof(T) == 8;
+    T wm0 = T(0), wm1 = T(0), wm2 = T(0), w00 = T(0), w01 = T(0), w02 = T(0);
+    T qm0 = T(0), qm1 = T(0), qm2 = T(0), q00 = T(0), q01 = T(0), q02 = T(0);   // their squares
+    if (interact) {
+        wm0 = s0[-Gm::WP - 1];
+        wm1 = s0[-Gm::WP];
+        wm2 = s0[-Gm::WP + 1];
+        w00 = s0[-1];
+        w01 = s0[0];
+        w02 = s0[1];
+        if (kSlideSquares) {
+            qm0 = mul_rn(wm0, wm0);
+            qm1 = mul_rn(wm1, wm1);
+            qm2 = mul_rn(wm2, wm2);
+            q00 = mul_rn(w00, w00);
+            q01 = mul_rn(w01, w01);
+            q02 = mul_rn(w02, w02);
+        }
+    }
+
+    bool bad = false;
+    T* o = dst + static_cast<long long>(y0 + ly0 + GY) * pitch + (x0 + tx + Gm::GX);
+#pragma unroll
+    for (int r = 0; r < Gm::ROWS; ++r, o += pitch) {
+        const int ly = ly0 + r;
+        const int x = x0 + tx, y = y0 + ly;
+        T wp0 = T(0), wp1 = T(0), wp2 = T(0), qp0 = T(0), qp1 = T(0), qp2 = T(0);
+        if (interact) {
+            const T* sr = s0 + (r + 1) * Gm::WP;
+            wp0 = sr[-1];
+            wp1 = sr[0];
+            wp2 = sr[1];
+            if (kSlideSquares) {
+                qp0 = mul_rn(wp0, wp0);
+                qp1 = mul_rn(wp1, wp1);
+                qp2 = mul_rn(wp2, wp2);
+            }
+        }
+        if (FAST || (x < nx && y < ny)) {
+            const T* q = sf + (ly + GY) * Gm::WB + (tx + Gm::HX);
+            T f[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) f[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
+
+            T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
+            if (interact) {
+                if (!kSlideSquares) {
+                    qp0 = mul_rn(wp0, wp0);
+                    qp1 = mul_rn(wp1, wp1);
+                    qp2 = mul_rn(wp2, wp2);
+                    qm0 = mul_rn(wm0, wm0);
+                    qm1 = mul_rn(wm1, wm1);
+                    qm2 = mul_rn(wm2, wm2);
+                    q00 = mul_rn(w00, w00);
+                    q01 = mul_rn(w01, w01);
+                    q02 = mul_rn(w02, w02);
+                }
+                force_q<T>(negGw, hA, omA, kGw, w01, w02, wp1, w00, wm1, wp2, wp0, wm0, wm2, q01, q02, qp1, q00,
+                           qm1, qp2, qp0, qm0, qm2, Fx, Fy, Qxx, Qyy, Qxy);
+            }
+
+            T out[9];
+            collide<T, !FAST>(R, f, Fx, Fy, Qxx, Qyy, Qxy, out);
+            if (!(out[0] == out[0])) bad = true;
+
+#pragma unroll
+            for (int a = 0; a < 9; ++a) o[a * plane] = out[a];
+            if (!FAST && border) ghost(o, x, y, out);
+        }
+        wm0 = w00; wm1 = w01; wm2 = w02;
+        w00 = wp0; w01 = wp1; w02 = wp2;
+        qm0 = q00; qm1 = q01; qm2 = q02;
+        q00 = qp0; q01 = qp1; q02 = qp2;
+    }
+    return bad;
+}
+
 // One kernel, two ways to find the work, both from a __grid_constant__
 // argument block: ONE = a single lattice (StepArgs: constants and tensor
 // maps; tile coordinates from the tile index); otherwise a BatchArgs over up
@@ -255,6 +414,10 @@ __device__ __forceinline__ const Phys<double>& phys_of(const BatchArgs<double>&,
 // NBUF = 2 makes the CTAs persistent with a two-stage TMA pipeline: while
 // tile k is collided, the box of tile k+1 streams into the other
 // shared-memory buffer.
+// Each tile takes one of two code paths, chosen once per tile: the fast
+// path (every node inside the lattice and off its border, G != 0, fixed
+// shear rates; the EOS fixed at compile time) has no per-node checks, the
+// general path handles the rest.  Both compute the same bits.
 template <typename T, int BX, int BY, int NT, int NBUF, bool ONE, typename Args>
 __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int ntiles, int parity,
                                           unsigned long long timeout_ns, const Args& a) {
@@ -340,7 +503,11 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
         const int interact = P.interact;
         const EosRegs<T> E(P);
         const T rho_ref = P.rho_ref;
-        bool bad = false;
+        const bool border = x0 < 2 || x0 + BX > nx - 2 || y0 < 2 || y0 + BY > ny - 2;
+        // the fast path: whole tile inside and off the border (so also no
+        // node beyond nx, ny), G != 0, fixed shear rates
+        const bool fast = interact && !P.var_visc && !border;
+        const int eos = P.eos;
 
         bool ok = mbar_wait_bounded(&bar[b], ph, timeout_ns);
         if (k == 0 && (P.flags & LBM_FLAG_TEST_FORCE_TIMEOUT)) {
@@ -349,42 +516,11 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
         }
 
         // ---- rho and psi of the tile and its ring (Eq. 10) ---------------
-        // A density outside the EOS's psi domain gives a negative radicand and
-        // a NaN psi (square root), which reaches every output of the owned
-        // node (F and Q are linear in psi, 0 x NaN is NaN): the collision's
-        // NaN check below records it.  Ring nodes beyond the lattice's
-        // ghost images feed no owned node.
         if (interact && ok) {
-            auto ring = [&](int i, int j) {
-                const T* q = sf + (j + 1) * Gm::WB + (i + Gm::HX - 1);
-                T g[9];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) g[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
-                sp[j * Gm::WP + i] = Fast<T>::sqrt(radicand_step(E, rho_ref + rho_dev(g)));
-            };
-            // rows ty, ty + TY, ... (unrolled where a thread owns several rows;
-            // the one-row shapes run under a tighter register bound); the two
-            // right-hand ring columns go to the threads the last row pass
-            // leaves idle when there are enough, so that no warp evaluates
-            // more ring nodes than the busiest row pass gives it
-            constexpr int K = (Gm::HP + Gm::TY - 1) / Gm::TY;
-            constexpr bool kMerge = Gm::ROWS > 1 && (K * Gm::TY - Gm::HP) * BX >= 2 * Gm::HP;
-            if constexpr (Gm::ROWS > 1) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int j = ty + k * Gm::TY;
-                    if (j < Gm::HP) {
-                        ring(tx, j);
-                    } else if (kMerge && k == K - 1) {
-                        const int e = (j - Gm::HP) * BX + tx;
-                        if (e < 2 * Gm::HP) ring(BX + (e & 1), e >> 1);
-                    }
-                }
-            } else {
-                for (int j = ty; j < Gm::HP; j += Gm::TY) ring(tx, j);
-            }
-            if (!kMerge)
-                for (int e = tid; e < 2 * Gm::HP; e += NT) ring(BX + (e & 1), e >> 1);
+            if (fast && eos == LBM_EOS_CS) psi_ring<Gm, LBM_EOS_CS>(sf, sp, E, rho_ref, tid, tx, ty);
+            else if (fast && eos == LBM_EOS_VDW) psi_ring<Gm, LBM_EOS_VDW>(sf, sp, E, rho_ref, tid, tx, ty);
+            else if (fast && eos == LBM_EOS_PR) psi_ring<Gm, LBM_EOS_PR>(sf, sp, E, rho_ref, tid, tx, ty);
+            else psi_ring<Gm, 0>(sf, sp, E, rho_ref, tid, tx, ty);
         }
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
@@ -397,7 +533,7 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
         if (NBUF == 2 && tid == 0 && t + static_cast<int>(gridDim.x) < ntiles) issue(t + gridDim.x, b ^ 1);
 
         // ---- collide and stream every owned node -------------------------
-        T* __restrict__ dst;
+        T* dst;
         long long plane;
         int pitch;
         if constexpr (ONE) {
@@ -413,108 +549,11 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
             plane = I->plane;
             pitch = I->pitch;
         }
-        const bool border = x0 < 2 || x0 + BX > nx - 2 || y0 < 2 || y0 + BY > ny - 2;
-        // periodic images in the ghost cells read by the neighbouring tiles
-        auto ghost = [&](T* o, int x, int y, const T (&v)[9]) {
-            const bool xl = x < 2, xr = x >= nx - 2, yl = y < 2, yr = y >= ny - 2;
-            if (!(xl || xr || yl || yr)) return;
-            const int oxs[3] = {0, xl ? nx : 0, xr ? -nx : 0};
-            const int oys[3] = {0, yl ? ny : 0, yr ? -ny : 0};
-            const bool hx[3] = {true, xl, xr};
-            const bool hy[3] = {true, yl, yr};
-            for (int iy = 0; iy < 3; ++iy)
-                for (int ix = 0; ix < 3; ++ix) {
-                    if (!(hx[ix] && hy[iy]) || (ix == 0 && iy == 0)) continue;
-                    T* g = o + static_cast<long long>(oys[iy]) * pitch + oxs[ix];
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) g[a * plane] = v[a];
-                }
-        };
-
-        // each thread owns ROWS consecutive rows of one column; the 3x3 psi
-        // neighbourhood slides down with it (three new loads per node)
         const Regs<T> R(P);
-        const T G = P.G, A = P.A;
-        const T negGw = -G * T(1.0 / 12.0), hA = T(0.5) * A, omA = T(1) - A;
-        const T kGw = P.kappa * G * T(1.0 / 24.0);
-        const int ly0 = ty * Gm::ROWS;
-        const T* s0 = sp + (ly0 + 1) * Gm::WP + (tx + 1);   // psi of node (tx, ly0)
-        // FP64 slides the squares of the window too (six FP64 products fewer
-        // per node); FP32 forms them per node, which keeps it to fewer
-        // registers and measured faster
-        constexpr bool kSlideSquares = sizeof(T) == 8;
-        T wm0 = T(0), wm1 = T(0), wm2 = T(0), w00 = T(0), w01 = T(0), w02 = T(0);
-        T qm0 = T(0), qm1 = T(0), qm2 = T(0), q00 = T(0), q01 = T(0), q02 = T(0);   // their squares
-        if (interact) {
-            wm0 = s0[-Gm::WP - 1];
-            wm1 = s0[-Gm::WP];
-            wm2 = s0[-Gm::WP + 1];
-            w00 = s0[-1];
-            w01 = s0[0];
-            w02 = s0[1];
-            if (kSlideSquares) {
-                qm0 = mul_rn(wm0, wm0);
-                qm1 = mul_rn(wm1, wm1);
-                qm2 = mul_rn(wm2, wm2);
-                q00 = mul_rn(w00, w00);
-                q01 = mul_rn(w01, w01);
-                q02 = mul_rn(w02, w02);
-            }
-        }
-
-#pragma unroll
-        for (int r = 0; r < Gm::ROWS; ++r) {
-            const int ly = ly0 + r;
-            const int x = x0 + tx, y = y0 + ly;
-            T wp0 = T(0), wp1 = T(0), wp2 = T(0), qp0 = T(0), qp1 = T(0), qp2 = T(0);
-            if (interact) {
-                const T* sr = s0 + (r + 1) * Gm::WP;
-                wp0 = sr[-1];
-                wp1 = sr[0];
-                wp2 = sr[1];
-                if (kSlideSquares) {
-                    qp0 = mul_rn(wp0, wp0);
-                    qp1 = mul_rn(wp1, wp1);
-                    qp2 = mul_rn(wp2, wp2);
-                }
-            }
-            if (x < nx && y < ny) {
-                const T* q = sf + (ly + GY) * Gm::WB + (tx + Gm::HX);
-                T f[9];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) f[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
-
-                T Fx = T(0), Fy = T(0), Qxx = T(0), Qyy = T(0), Qxy = T(0);
-                if (interact) {
-                    if (!kSlideSquares) {
-                        qp0 = mul_rn(wp0, wp0);
-                        qp1 = mul_rn(wp1, wp1);
-                        qp2 = mul_rn(wp2, wp2);
-                        qm0 = mul_rn(wm0, wm0);
-                        qm1 = mul_rn(wm1, wm1);
-                        qm2 = mul_rn(wm2, wm2);
-                        q00 = mul_rn(w00, w00);
-                        q01 = mul_rn(w01, w01);
-                        q02 = mul_rn(w02, w02);
-                    }
-                    force_q<T>(negGw, hA, omA, kGw, w01, w02, wp1, w00, wm1, wp2, wp0, wm0, wm2, q01, q02, qp1, q00,
-                               qm1, qp2, qp0, qm0, qm2, Fx, Fy, Qxx, Qyy, Qxy);
-                }
-
-                T out[9];
-                collide<T>(R, f, Fx, Fy, Qxx, Qyy, Qxy, out);
-                if (!(out[0] == out[0])) bad = true;
-
-                T* o = dst + static_cast<long long>(y + GY) * pitch + (x + Gm::GX);
-#pragma unroll
-                for (int a = 0; a < 9; ++a) o[a * plane] = out[a];
-                if (border) ghost(o, x, y, out);
-            }
-            wm0 = w00; wm1 = w01; wm2 = w02;
-            w00 = wp0; w01 = wp1; w02 = wp2;
-            qm0 = q00; qm1 = q01; qm2 = q02;
-            q00 = qp0; q01 = qp1; q02 = qp2;
-        }
+        const bool bad = fast ? collide_rows<Gm, true>(sf, sp, P, R, dst, plane, pitch, x0, y0, nx, ny, border,
+                                                       interact, tx, ty)
+                              : collide_rows<Gm, false>(sf, sp, P, R, dst, plane, pitch, x0, y0, nx, ny, border,
+                                                        interact, tx, ty);
         if (bad) atomicOr(status, ST_UNSTABLE);
     }
 }
