@@ -205,6 +205,30 @@ template <int EOSK, typename T> __device__ __forceinline__ T radicand_step(const
     return P.two_over_G * fma(rho, T(-1.0 / 3.0), p);
 }
 
+// psi of Eq. 10 for the Carnahan-Starling law in FP64, with the division by
+// q^3 = (1 - b rho/4)^3 and the square root folded into one reciprocal
+// square root: with W = (2/G) rho [K R T num - (K a rho + 1/3) q^3] (num the
+// law's numerator polynomial), psi^2 = W / q^3, so psi = W / sqrt(W q^3).
+// 1/(2 sqrt(x)) comes from the hardware estimate refined by two Goldschmidt
+// steps, as in Fast<double>::sqrt.  kR = (2/G) K R T, kA = (2/G) K a,
+// k3 = (2/G)/3.  A negative radicand gives NaN (as the square root does),
+// psi(W = 0) = 0.
+__device__ __forceinline__ double psi_cs_fp64(double b4, double kR, double kA, double k3, double rho) {
+    const double n = b4 * rho, q = 1.0 - n;
+    const double num = fma(n, fma(n, 1.0 - n, 1.0), 1.0);
+    const double q3 = q * q * q;
+    const double W = rho * fma(-fma(kA, rho, k3), q3, kR * num);
+    const double x = W * q3;
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double g0 = x * y, h0 = 0.5 * y;
+    const double r0 = fma(-g0, h0, 0.5);
+    const double g1 = fma(g0, r0, g0), h1 = fma(h0, r0, h0);
+    const double r1 = fma(-g1, h1, 0.5);
+    const double h2 = fma(h1, r1, h1);
+    return W == 0.0 ? 0.0 : (W + W) * h2;
+}
+
 // Hybrid force (Eq. 9) and modifying tensor (Eq. 23, x G/2) of one node
 // from psi at the node (p0) and its eight neighbours (p_a at x + e_a).
 // The lattice sums are formed with the integer weights 12 w_a (4 on the
@@ -259,12 +283,24 @@ template <typename Gm, int EOSK, typename T>
 __device__ __forceinline__ void psi_ring(const T* sf, T* sp, const EosRegs<T>& E, T rho_ref, int tid, int tx,
                                          int ty) {
     constexpr int BX = Gm::BX;
+    // FP64 Carnahan-Starling: psi_cs_fp64 on every path (the law fixed at
+    // compile time or read at run time), so that every tile computes the same bits
+    const bool cs64 = sizeof(T) == 8 && (EOSK ? EOSK : E.eos) == LBM_EOS_CS;
+    const T kR = E.two_over_G * E.K * E.RT, kA = E.two_over_G * E.K * E.a, k3 = E.two_over_G * T(1.0 / 3.0);
     auto ring = [&](int i, int j) {
         const T* q = sf + (j + 1) * Gm::WB + (i + Gm::HX - 1);
         T g[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) g[a] = q[a * Gm::PB - cy(a) * Gm::WB - cx(a)];
-        sp[j * Gm::WP + i] = Fast<T>::sqrt(radicand_step<EOSK>(E, rho_ref + rho_dev(g)));
+        const T rho = rho_ref + rho_dev(g);
+        T psi;
+        if constexpr (sizeof(T) == 8) {
+            if (cs64) psi = psi_cs_fp64(E.b4, kR, kA, k3, rho);
+            else psi = Fast<T>::sqrt(radicand_step<EOSK>(E, rho));
+        } else {
+            psi = Fast<T>::sqrt(radicand_step<EOSK>(E, rho));
+        }
+        sp[j * Gm::WP + i] = psi;
     };
     // rows ty, ty + TY, ... (unrolled where a thread owns several rows; the
     // one-row shapes run under a tighter register bound); the two right-hand
@@ -293,10 +329,11 @@ __device__ __forceinline__ void psi_ring(const T* sf, T* sp, const EosRegs<T>& E
 
 // Force, modifying tensor, collision and store of the thread's ROWS nodes
 // (consecutive rows of column tx).  Returns true when a node's results are
-// NaN.  FAST: every node of the tile lies inside the lattice and away from
-// its two border rows and columns (no bounds checks, no ghost images), G != 0
-// and the shear rates are fixed; decided once per tile.
-template <typename Gm, bool FAST, typename T, typename RP>
+// NaN.  FAST: every node of the tile lies inside the lattice (no bounds
+// checks), G != 0 and the shear rates are fixed; GHOST: the tile is within
+// two rows or columns of the lattice's edge, so its nodes there also write
+// their periodic images.  Both are decided once per tile.
+template <typename Gm, bool FAST, bool GHOST, typename T, typename RP>
 __device__ __forceinline__ bool collide_rows(const T* sf, const T* sp, const Phys<T>& P, const RP& R, T* __restrict__ dst,
                                              long long plane, int pitch, int x0, int y0, int nx, int ny, bool border,
                                              bool interact_rt, int tx, int ty) {
@@ -395,7 +432,7 @@ __device__ __forceinline__ bool collide_rows(const T* sf, const T* sp, const Phy
 
 #pragma unroll
             for (int a = 0; a < 9; ++a) o[a * plane] = out[a];
-            if (!FAST && border) ghost(o, x, y, out);
+            if (GHOST && border) ghost(o, x, y, out);
         }
         wm0 = w00; wm1 = w01; wm2 = w02;
         w00 = wp0; w01 = wp1; w02 = wp2;
@@ -414,10 +451,11 @@ __device__ __forceinline__ bool collide_rows(const T* sf, const T* sp, const Phy
 // NBUF = 2 makes the CTAs persistent with a two-stage TMA pipeline: while
 // tile k is collided, the box of tile k+1 streams into the other
 // shared-memory buffer.
-// Each tile takes one of two code paths, chosen once per tile: the fast
-// path (every node inside the lattice and off its border, G != 0, fixed
-// shear rates; the EOS fixed at compile time) has no per-node checks, the
-// general path handles the rest.  Both compute the same bits.
+// Each tile takes one of three code paths, chosen once per tile: the fast
+// path (every node inside the lattice, G != 0, fixed shear rates; the EOS
+// fixed at compile time) has no per-node checks, in two copies: with and
+// without the periodic ghost images of tiles at the lattice's edge; the
+// general path handles the rest.  All compute the same bits.
 template <typename T, int BX, int BY, int NT, int NBUF, bool ONE, typename Args>
 __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int ntiles, int parity,
                                           unsigned long long timeout_ns, const Args& a) {
@@ -504,9 +542,9 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
         const EosRegs<T> E(P);
         const T rho_ref = P.rho_ref;
         const bool border = x0 < 2 || x0 + BX > nx - 2 || y0 < 2 || y0 + BY > ny - 2;
-        // the fast path: whole tile inside and off the border (so also no
-        // node beyond nx, ny), G != 0, fixed shear rates
-        const bool fast = interact && !P.var_visc && !border;
+        // the fast path: every node of the tile inside the lattice, G != 0,
+        // fixed shear rates
+        const bool fast = interact && !P.var_visc && x0 + BX <= nx && y0 + BY <= ny;
         const int eos = P.eos;
 
         bool ok = mbar_wait_bounded(&bar[b], ph, timeout_ns);
@@ -550,10 +588,16 @@ __device__ __forceinline__ void step_body(const Inst* __restrict__ insts, int nt
             pitch = I->pitch;
         }
         const Regs<T> R(P);
-        const bool bad = fast ? collide_rows<Gm, true>(sf, sp, P, R, dst, plane, pitch, x0, y0, nx, ny, border,
-                                                       interact, tx, ty)
-                              : collide_rows<Gm, false>(sf, sp, P, R, dst, plane, pitch, x0, y0, nx, ny, border,
-                                                        interact, tx, ty);
+        bool bad;
+        if (fast && !border)
+            bad = collide_rows<Gm, true, false>(sf, sp, P, R, dst, plane, pitch, x0, y0, nx, ny, border, interact,
+                                                tx, ty);
+        else if (fast)
+            bad = collide_rows<Gm, true, true>(sf, sp, P, R, dst, plane, pitch, x0, y0, nx, ny, border, interact, tx,
+                                               ty);
+        else
+            bad = collide_rows<Gm, false, true>(sf, sp, P, R, dst, plane, pitch, x0, y0, nx, ny, border, interact,
+                                                tx, ty);
         if (bad) atomicOr(status, ST_UNSTABLE);
     }
 }
