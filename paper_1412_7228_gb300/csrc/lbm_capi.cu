@@ -11,6 +11,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm_eos_host.h"
 #include "lbm_internal.cuh"
 
@@ -19,6 +21,15 @@ using lbm::Inst;
 namespace {
 
 constexpr unsigned long long kTimeoutNs = 1000000000ull;   // bounded TMA wait: 1 s
+
+// An NVTX range over the enclosing scope (host side: it brackets the calls
+// that enqueue or wait for the work); a no-op unless a profiler is attached.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 constexpr int kGraphSteps = 32;                            // steps per captured graph (even)
 
 // The TMA tensor maps of one instance's two time levels (host copies; the
@@ -818,6 +829,7 @@ int lbm_batch_init_density(lbm_ctx* c, int i, const double* rho, const double* u
     if (rc) return rc;
     if (!rho) return fail(c, LBM_EINVAL, "rho must not be NULL%s");
     if (!c->hp[i].set) return fail(c, LBM_EINVAL, "set the parameters before the density%s");
+    Range range("lbm_batch_init_density");
     const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
     // the EOS range only matters when psi is evaluated (G != 0)
     const double rmax = c->hp[i].G != 0.0 ? eos_rho_max(c->hp[i].eos) : HUGE_VAL;
@@ -849,6 +861,7 @@ int lbm_init_density(lbm_ctx* c, const double* rho, const double* ux, const doub
 
 int lbm_step(lbm_ctx* c, int n) {
     if (!c || n < 0) return LBM_EINVAL;
+    Range range("lbm_step");
     int rc = ready(c);
     if (rc) return rc;
     CK(c, cudaSetDevice(c->device));
@@ -856,6 +869,7 @@ int lbm_step(lbm_ctx* c, int n) {
         while (n >= kGraphSteps) {
             rc = ensure_graph(c, c->parity);
             if (rc) return rc;
+            Range replay("lbm_step: graph replay");
             CK(c, cudaGraphLaunch(c->gexec[c->parity], c->stream));
             c->launches += static_cast<long long>(kGraphSteps) * step_launches(c);
             c->steps += kGraphSteps;
@@ -892,6 +906,7 @@ int lbm_batch_read_fields(lbm_ctx* c, int i, double* rho, double* ux, double* uy
     int rc = check_idx(c, i);
     if (rc) return rc;
     if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
+    Range range("lbm_batch_read_fields");
     CK(c, cudaSetDevice(c->device));
     const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
     double* outs[4] = {rho, ux, uy, psi};
@@ -934,6 +949,7 @@ int lbm_batch_measure(lbm_ctx* c, int i, double cxc, double cyc, double r_in, do
     if (rc) return rc;
     if (!out || !(r_in >= 0) || !(r_out >= 0)) return fail(c, LBM_EINVAL, "bad measurement arguments%s");
     if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
+    Range range("lbm_batch_measure");
     CK(c, cudaSetDevice(c->device));
     CK(c, lbm::aux_measure(c->h[i], c->d_inst + i, c->parity, cxc, cyc, r_in, r_out, c->d_partials, c->d_result,
                            c->stream));
@@ -969,6 +985,7 @@ int lbm_batch_stats(lbm_ctx* c, int i, double* out5) {
     if (rc) return rc;
     if (!out5) return fail(c, LBM_EINVAL, "out must not be NULL%s");
     if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
+    Range range("lbm_batch_stats");
     CK(c, cudaSetDevice(c->device));
     CK(c, lbm::aux_stats(c->h[i], c->d_inst + i, c->parity, c->d_partials, c->d_result, c->stream));
     double s[lbm::kReduceSlots];
@@ -1102,6 +1119,7 @@ int lbm_set_schedule(lbm_ctx* c, int tile_config, int schedule) {
 
 int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double* ms_per_step) {
     if (!c || steps < 1) return LBM_EINVAL;
+    Range range("lbm_autotune");
     int rc = ready(c);
     if (rc) return rc;
     rc = sync_all(c);

@@ -104,13 +104,60 @@ def _harvest(batch: L.Batch, i: int, d: Droplet, acc: Optional[List[Dict]] = Non
     d.umax = batch.stats(i)["umax"]
 
 
+class Trace:
+    """Per-run JSON-lines trace of the FP64 reductions (lbm_batch_stats):
+    every `every` steps one line per instance with the step, the instance,
+    its mass, momentum, kinetic energy, peak speed and status, so that a long
+    sweep leaves a record of conservation and of spurious currents."""
+
+    def __init__(self, path: str, every: int):
+        if every < 1:
+            raise ValueError("the trace interval must be at least one step")
+        self.fh = open(path, "a")
+        self.every = every
+        self.seconds = 0.0
+
+    def record(self, batch: L.Batch, step: int):
+        t = time.perf_counter()
+        for i in range(batch.n):
+            st = batch.status(i)
+            rec = {"step": step, "instance": i, "status": st}
+            if st == L.LBM_OK:
+                rec.update(batch.stats(i))
+            self.fh.write(json.dumps(rec) + "\n")
+        self.fh.flush()
+        self.seconds += time.perf_counter() - t
+
+    def close(self):
+        self.fh.close()
+
+
+def _advance(batch: L.Batch, n: int, done: int, trace: Optional[Trace]) -> int:
+    """Step n times; with a trace, stop at every multiple of its interval to
+    record it.  Returns the steps done."""
+    if trace is None:
+        batch.step(n)
+        return done + n
+    end = done + n
+    while done < end:
+        k = min(end, (done // trace.every + 1) * trace.every) - done
+        batch.step(k)
+        done += k
+        if done % trace.every == 0:
+            trace.record(batch, done)
+    return done
+
+
 def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP32, autotune: bool = True,
               graphs: bool = True, s=S_DEFAULT, schedule: Optional[Tuple[int, int]] = None,
-              window: Optional[Tuple[int, int]] = None) -> Dict:
+              window: Optional[Tuple[int, int]] = None, trace: Optional[str] = None,
+              trace_every: int = 1000) -> Dict:
     """Step every droplet together; fill in the per-droplet results.
     schedule: (tile configuration, CTA schedule) instead of autotuning.
     window: (span, every): Laplace sampling averaged over the last `span`
-    steps, one sample every `every` steps (None: one sample at the end)."""
+    steps, one sample every `every` steps (None: one sample at the end).
+    trace: append a JSON-lines record of every instance's reductions every
+    trace_every steps to this file (Trace)."""
     import torch
     batch = L.Batch([d.L for d in droplets], [d.L for d in droplets], precision)
     for i, d in enumerate(droplets):
@@ -126,21 +173,24 @@ def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP
     span, every = window if window else (0, 1)
     if span >= steps or span % every:
         raise ValueError("the window must be a whole number of sampling intervals shorter than the run")
+    tr = Trace(trace, trace_every) if trace else None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sample_s = 0.0
-    batch.step(steps - span)
+    done = _advance(batch, steps - span, 0, tr)
     if window:
         acc = [[] for _ in droplets]
         for k in range(span // every + 1):
             if k:
-                batch.step(every)
+                done = _advance(batch, every, done, tr)
             t1 = time.perf_counter()
             for i, d in enumerate(droplets):
                 acc[i].append(_sample(batch, i, d))
             sample_s += time.perf_counter() - t1
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0 - sample_s
+    dt = time.perf_counter() - t0 - sample_s - (tr.seconds if tr else 0.0)
+    if tr:
+        tr.close()
     launches = batch.kernel_launches
     for i, d in enumerate(droplets):
         _harvest(batch, i, d, acc[i] if acc else None)
@@ -201,9 +251,11 @@ def in_equilibrium(d: Droplet, max_drift: float = 1e-3) -> bool:
 
 def laplace_sweep(radii=(20, 30, 40, 50, 60), kappas=(0.0, 0.1, 0.3, 0.5), t_over_tc=(0.6, 0.7, 0.8), L_=256,
                   steps=30000, A=-0.85, precision=L.LBM_FP32, autotune=True,
-                  window=(WINDOW_STEPS, WINDOW_EVERY)) -> Tuple[List[LaplaceFit], Dict]:
+                  window=(WINDOW_STEPS, WINDOW_EVERY), trace: Optional[str] = None,
+                  trace_every: int = 1000) -> Tuple[List[LaplaceFit], Dict]:
     drops = [Droplet(L_, float(R), tr, A, k) for tr in t_over_tc for k in kappas for R in radii]
-    info = run_batch(drops, steps, precision, autotune=autotune, window=window)
+    info = run_batch(drops, steps, precision, autotune=autotune, window=window, trace=trace,
+                     trace_every=trace_every)
     info["droplets"] = [{k: getattr(d, k) for k in ("radius", "t_over_tc", "kappa", "dp", "R_eq", "rho_l", "rho_g",
                                                      "umax", "status", "R_drift")} for d in drops]
     fits = []
@@ -242,10 +294,15 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--trace", default=None, metavar="PATH",
+                    help="append a JSON-lines trace of every instance's mass, momentum, kinetic energy and peak "
+                         "speed (Laplace sweep)")
+    ap.add_argument("--trace-every", type=int, default=1000)
     args = ap.parse_args(argv)
     prec = L.LBM_FP32 if args.precision == "fp32" else L.LBM_FP64
     if args.laplace:
-        fits, info = laplace_sweep(steps=args.steps or 30000, precision=prec)
+        fits, info = laplace_sweep(steps=args.steps or 30000, precision=prec, trace=args.trace,
+                                   trace_every=args.trace_every)
         out = {"sweep": "laplace", "precision": args.precision, "seconds": info["seconds"], "mlups": info["mlups"],
                "fits": [f.__dict__ for f in fits], "droplets": info.get("droplets")}
         print(json.dumps(out))
