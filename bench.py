@@ -250,6 +250,34 @@ def time_steps(torch, lat, steps):
     return e0.elapsed_time(e1) / 1000.0
 
 
+def plain_method_64(torch, P, steps=10000):
+    """The plain-method workload in full on the GPU: a 64x64 static droplet
+    (R0 = 15, tanh width 2 between the Maxwell densities), Carnahan-Starling
+    at 0.7 Tc, A = -0.85, kappa = 0, 10^4 steps, FP32 and FP64, each with its
+    autotuned tile and graphs, timed with CUDA events.  It fits in L2 and
+    is latency-bound: wall time, no roofline claim."""
+    import lbm_inputs as I
+    eos = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
+    _, Tc, _ = P.lbm_eos_critical(eos)
+    eos.T = TR_CFG * Tc
+    rg, rl, _ = P.lbm_eos_maxwell(eos)
+    rho0 = I.droplet_density(64, 64, 15.0, rl, rg)
+    out = {"workload": "64x64 static droplet R0 = 15, kappa = 0, 10^4 steps (fits in L2: no roofline claim)"}
+    for name, prec in (("fp32", P.LBM_FP32), ("fp64", P.LBM_FP64)):
+        lat = P.Lattice(64, 64, prec)
+        lat.set_params(eos, A_CFG, 0.0, G=-1.0, s=S_CFG, rho_ref=rg)
+        lat.init_density(rho0)
+        k, sch, _ = lat.autotune(20)
+        lat.init_density(rho0)
+        lat.use_graphs(True)
+        t = time_steps(torch, lat, steps)
+        lat.sync()
+        lat.close()
+        out[name] = {"seconds": t, "us_per_step": t / steps * 1e6, "mlups": 64 * 64 * steps / t / 1e6,
+                     "tile": list(P.lbm_tile_configs(prec)[k])}
+    return out
+
+
 def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
     """The batched uneven sweep workload (64 static droplets, L uniform over
     {128, 256, 512, 1024}, R0 = 0.2 L, T/Tc ~ U[0.6, 0.85], kappa ~ U[0, 0.6],
@@ -340,6 +368,46 @@ def cpu_oracle_mlups(nx, ny, steps):
     O.step(p, f, 1)
     t0 = time.perf_counter()
     O.step(p, f, steps)
+    dt = time.perf_counter() - t0
+    return nx * ny * steps / dt / 1e6, dt
+
+
+def cpu_oracle_droplet64(steps=10000):
+    """The plain-method workload in full on the FP64 oracle, single thread:
+    a 64x64 static droplet (R0 = 15 at the centre, tanh width 2 between the
+    Maxwell densities), Carnahan-Starling at 0.7 Tc, A = -0.85, kappa = 0,
+    10^4 steps.  Returns (MLUPS, seconds)."""
+    import warnings
+    warnings.filterwarnings("ignore")
+    import lbm_inputs as I
+    import oracle as O
+    from oracle import analysis as An
+    base = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, A=A_CFG, kappa=0.0, G=-1.0, s=list(S_CFG))
+    _, Tc, _ = An.critical_point(base)
+    p = An.with_T(base, TR_CFG * Tc)
+    rg, rl, _ = An.maxwell(p)
+    f = O.init_equilibrium(I.droplet_density(64, 64, 15.0, rl, rg))
+    t0 = time.perf_counter()
+    O.step(p, f, steps)
+    dt = time.perf_counter() - t0
+    return 64 * 64 * steps / dt / 1e6, dt
+
+
+def cpu_oracle_all_cores(nx, ny, steps, threads):
+    """The OpenMP build of the FP64 oracle (same bits as the serial one) on
+    all host cores, on the same sample as cpu_oracle_mlups."""
+    import warnings
+    warnings.filterwarnings("ignore")
+    import lbm_inputs as I
+    import oracle as O
+    from oracle import analysis as An
+    base = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, A=A_CFG, kappa=KAPPA_CFG, G=-1.0, s=list(S_CFG))
+    _, Tc, _ = An.critical_point(base)
+    p = An.with_T(base, TR_CFG * Tc)
+    f = O.init_equilibrium(I.spinodal_density(nx, ny, RHO0, 0.01, SEED))
+    O.step(p, f, 1, threads=threads)
+    t0 = time.perf_counter()
+    O.step(p, f, steps, threads=threads)
     dt = time.perf_counter() - t0
     return nx * ny * steps / dt / 1e6, dt
 
@@ -526,6 +594,11 @@ def run_ours(args):
                "h2d_bytes_per_step": 8 * N / args.steps, "d2h_bytes_per_step": 8 * N / args.steps,
                "what": "lbm_init_density from pinned host rho, lbm_step(K), lbm_read_fields(rho) to host"}
 
+    # ---- the plain-method workload in full: 64^2 droplet, 10^4 steps --------
+    plain = None
+    if not args.no_workloads:
+        plain = plain_method_64(torch, P)
+
     # ---- batched uneven sweep against the same lattices one after another ---
     batched = None
     if not args.no_sweep:
@@ -539,6 +612,14 @@ def run_ours(args):
                "sample": "%d steps of a %dx%d periodic sample of the workload (%.1f s), FP64 single-thread"
                          % (args.cpu_steps, cn, cn, dt),
                "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
+        nth = os.cpu_count() or 1
+        ma, dta = cpu_oracle_all_cores(cn, cn, args.cpu_steps, nth)
+        cpu["all_cores"] = {"value": ma, "unit": "MLUPS", "cores": nth, "seconds": dta,
+                            "sample": "the same sample, OpenMP build of the oracle (same bits)"}
+        md, dtd = cpu_oracle_droplet64()
+        cpu["plain_method_64x64"] = {"value": md, "unit": "MLUPS", "cores": 1, "seconds": dtd,
+                                     "sample": "64x64 static droplet R0 = 15, kappa = 0, 10^4 steps: the whole "
+                                               "plain-method workload, FP64 oracle, single thread"}
 
     if rank == 0:
         line = {
@@ -549,7 +630,8 @@ def run_ours(args):
             "config": workload_config(nx, ny, args.precision, dict(
                 {"tile": list(tile), "parallelism": "replicas" if ws > 1 else "single"}, **graph_use(args.steps))),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": launches, "fp64": fp64, "other_workloads": others, "batched_sweep": batched,
+            "gpu_launches": launches, "fp64": fp64, "other_workloads": others, "plain_method_64x64": plain,
+            "batched_sweep": batched,
             "status_ok": status_ok,
         }
         print(json.dumps(line), flush=True)

@@ -228,11 +228,21 @@ int lbm_tile_config_count(int precision);
 int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads, int* stages);
 /* Select tile configuration k and CTA schedule (0: instance-major row
  * order, 1: the tiles of each launch's instances interleaved, 2: largest
- * instance first).  A batch is stepped by one launch per 64 instances. */
+ * instance first; a batch is stepped by one launch per 64 instances and
+ * step).  Schedule 3 steps every instance through all n steps of an
+ * lbm_step(n) call in one persistent launch per 32 instances: CTAs take
+ * (step, tile) items in step order from a counter in device memory and start
+ * step s of a tile once every tile within two nodes of it (periodic) has
+ * finished step s - 1 (each dependency wait bounded; one that gives up reports
+ * LBM_ETIMEOUT); the launch is cooperative (every CTA resident), needs a
+ * tile configuration of one tile box per CTA (stages 1; LBM_EINVAL
+ * otherwise), and CUDA graphs are not used with it.  Every schedule gives the
+ * same bits. */
 int lbm_set_schedule(lbm_ctx* ctx, int tile_config, int schedule);
 /* Time every (tile configuration, schedule) pair over `steps` steps of the
- * current state (which is restored afterwards) and keep the fastest.
- * Writes the choice and its time per step in milliseconds. */
+ * current state (which is restored afterwards) and keep the fastest (one
+ * lattice: schedules 0 and 3).  Writes the choice and its time per step in
+ * milliseconds. */
 int lbm_autotune(lbm_ctx* ctx, int steps, int* tile_config, int* schedule, double* ms_per_step);
 
 /* CUDA graphs for lbm_step: on (1) or off (0, the default). */

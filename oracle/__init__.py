@@ -18,6 +18,7 @@ import numpy as np
 from . import build as _build
 
 _lib = None
+_lib_omp = None
 
 EOS_CS, EOS_VDW, EOS_PR = 1, 2, 3
 
@@ -80,31 +81,45 @@ class Params:
         return p
 
 
-def lib():
-    global _lib
+def lib(threads: int = 1):
+    """The oracle library; threads > 1 selects its OpenMP build (same bits)
+    with that many threads."""
+    global _lib, _lib_omp
+    if threads > 1:
+        if _lib_omp is None:
+            _build.build()
+            _lib_omp = _bind(ctypes.CDLL(_build.LIB_OMP))
+        _lib_omp.orc_threads(int(threads))
+        return _lib_omp
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        dp = ctypes.POINTER(ctypes.c_double)
-        ip = ctypes.POINTER(ctypes.c_int)
-        pp = ctypes.POINTER(_Params)
-        L.orc_matrices.argtypes = [dp, dp]
-        L.orc_velocities.argtypes = [ip, ip, dp]
-        L.orc_pressure.argtypes = [pp, ctypes.c_double]
-        L.orc_pressure.restype = ctypes.c_double
-        L.orc_pressure_array.argtypes = [pp, dp, dp, ctypes.c_long]
-        L.orc_meq.argtypes = [ctypes.c_double] * 3 + [dp]
-        L.orc_source_s.argtypes = [ctypes.c_double] * 4 + [dp]
-        L.orc_source_c.argtypes = [pp] + [ctypes.c_double] * 3 + [dp]
-        L.orc_force_q.argtypes = [pp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp]
-        L.orc_collide_node.argtypes = [pp, dp] + [ctypes.c_double] * 5 + [dp]
-        L.orc_init_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
-        L.orc_macro.argtypes = [pp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_macro.restype = ctypes.c_int
-        L.orc_step.argtypes = [pp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int]
-        L.orc_step.restype = ctypes.c_int
-        _lib = L
+        _build.build()
+        _lib = _bind(ctypes.CDLL(_build.LIB))
     return _lib
+
+
+def _bind(L):
+    """Argument and result types of the oracle's C functions."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    pp = ctypes.POINTER(_Params)
+    L.orc_matrices.argtypes = [dp, dp]
+    L.orc_velocities.argtypes = [ip, ip, dp]
+    L.orc_pressure.argtypes = [pp, ctypes.c_double]
+    L.orc_pressure.restype = ctypes.c_double
+    L.orc_pressure_array.argtypes = [pp, dp, dp, ctypes.c_long]
+    L.orc_meq.argtypes = [ctypes.c_double] * 3 + [dp]
+    L.orc_source_s.argtypes = [ctypes.c_double] * 4 + [dp]
+    L.orc_source_c.argtypes = [pp] + [ctypes.c_double] * 3 + [dp]
+    L.orc_force_q.argtypes = [pp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+    L.orc_collide_node.argtypes = [pp, dp] + [ctypes.c_double] * 5 + [dp]
+    L.orc_init_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+    L.orc_macro.argtypes = [pp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_macro.restype = ctypes.c_int
+    L.orc_step.argtypes = [pp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int]
+    L.orc_step.restype = ctypes.c_int
+    L.orc_threads.argtypes = [ctypes.c_int]
+    L.orc_threads.restype = ctypes.c_int
+    return L
 
 
 def _dp(a: np.ndarray):
@@ -189,12 +204,13 @@ class OracleUnstable(RuntimeError):
     pass
 
 
-def step(p: Params, f: np.ndarray, n: int) -> np.ndarray:
-    """Advance f (shape (9, ny, nx), modified in place) by n time steps."""
+def step(p: Params, f: np.ndarray, n: int, threads: int = 1) -> np.ndarray:
+    """Advance f (shape (9, ny, nx), modified in place) by n time steps;
+    threads > 1 runs the OpenMP build (same bits)."""
     assert f.dtype == np.float64 and f.flags["C_CONTIGUOUS"] and f.shape[0] == 9
     _, ny, nx = f.shape
     pc = p.c()
-    rc = lib().orc_step(ctypes.byref(pc), nx, ny, _dp(f), int(n))
+    rc = lib(threads).orc_step(ctypes.byref(pc), nx, ny, _dp(f), int(n))
     if rc == 1:
         raise OracleUnstable("density left the psi domain of the EOS or became NaN")
     if rc != 0:

@@ -10,6 +10,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lbm_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 OPC_SRC = os.path.join(HERE, "op_count.cpp")
 OPC_BIN = os.path.join(HERE, "op_count")
 
@@ -19,17 +20,19 @@ def _stale(out: str, *srcs: str) -> bool:
 
 
 def build(force: bool = False) -> str:
-    """liboracle.so, and the operation counter op_count (lbm_oracle.c traced
-    in C++, see op_count.cpp)."""
-    if force or _stale(LIB, SRC):
-        tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
+    """liboracle.so, its OpenMP build liboracle_omp.so (same source, same
+    bits, nodes shared among threads), and the operation counter op_count
+    (lbm_oracle.c traced in C++, see op_count.cpp)."""
+    for out, extra in ((LIB, ["-Wno-unknown-pragmas"]), (LIB_OMP, ["-fopenmp"])):
+        if force or _stale(out, SRC):
+            tmp = out + ".tmp%d" % os.getpid()
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                   "-shared", "-Wall", "-Wextra"] + extra + ["-o", tmp, SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, out)
     if force or _stale(OPC_BIN, SRC, OPC_SRC):
         tmp = OPC_BIN + ".tmp%d" % os.getpid()
-        subprocess.run(["g++", "-O1", "-std=c++17", "-Wall", "-o", tmp, OPC_SRC], check=True)
+        subprocess.run(["g++", "-O1", "-std=c++17", "-Wall", "-Wno-unknown-pragmas", "-o", tmp, OPC_SRC], check=True)
         os.replace(tmp, OPC_BIN)
     return LIB
 

@@ -20,6 +20,12 @@
  * Storage: f[a*ny*nx + y*nx + x] holds the pre-collision population f_a(x,t)
  * of node (x, y); x is the fastest index.
  *
+ * Threads: the per-node loops carry OpenMP work-sharing pragmas.  Built
+ * without -fopenmp (liboracle.so) they are ignored; built with it
+ * (liboracle_omp.so) the nodes of a loop are shared among threads.  Every
+ * node's arithmetic is the same either way and no loop accumulates across
+ * nodes, so both builds give the same bits.
+ *
  * Readings of the paper taken here (each is pinned by a CPU test):
  *  R1  The paper does not print M.  Its moment order (rho, e, eps, j_x, q_x,
  *      j_y, q_y, p_xx, p_xy) in Eq. 4 is that of Lallemand & Luo, whose rows
@@ -41,6 +47,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q9 9
 
@@ -190,6 +199,7 @@ void orc_source_c(const orc_params *p, double Qxx, double Qyy, double Qxy, doubl
  * scaled by G/2 per R3) from a given psi field, periodic in x and y. */
 void orc_force_q(const orc_params *p, int nx, int ny, const double *psi,
                  double *Fx, double *Fy, double *Qxx, double *Qyy, double *Qxy) {
+#pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long i = (long)y * nx + x;
@@ -295,6 +305,7 @@ void orc_init_equilibrium(int nx, int ny, const double *rho, const double *ux,
 static int rho_psi(const orc_params *p, int nx, int ny, const double *f, double *rho, double *psi) {
     long N = (long)nx * ny;
     int ok = 1;
+#pragma omp parallel for reduction(&:ok)
     for (long i = 0; i < N; ++i) {
         double r = 0.0;
         for (int a = 0; a < Q9; ++a) r += f[a * N + i];
@@ -370,6 +381,7 @@ int orc_step(const orc_params *p, int nx, int ny, double *f, int nsteps) {
     for (int t = 0; t < nsteps; ++t) {
         if (!rho_psi(p, nx, ny, f, rho, psi)) { rc = 1; break; }
         forces(p, nx, ny, psi, Fx, Fy, Qxx, Qyy, Qxy);
+#pragma omp parallel for
         for (long i = 0; i < N; ++i) {
             double fn[Q9], fo[Q9];
             for (int a = 0; a < Q9; ++a) fn[a] = f[a * N + i];
@@ -377,7 +389,9 @@ int orc_step(const orc_params *p, int nx, int ny, double *f, int nsteps) {
             for (int a = 0; a < Q9; ++a) fpost[a * N + i] = fo[a];
         }
         /* streaming: f_a(x + e_a, t+1) = f*_a(x, t), periodic in x and y
-         * (or half-way bounce-back at the two y walls in the test-only mode) */
+         * (or half-way bounce-back at the two y walls in the test-only mode);
+         * every target is written by exactly one source */
+#pragma omp parallel for
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
                 for (int a = 0; a < Q9; ++a) {
@@ -394,4 +408,15 @@ int orc_step(const orc_params *p, int nx, int ny, double *f, int nsteps) {
     }
     free(work);
     return rc;
+}
+
+/* Threads of the OpenMP build (n > 0 sets them); 1 without OpenMP. */
+int orc_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

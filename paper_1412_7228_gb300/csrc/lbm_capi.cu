@@ -59,7 +59,7 @@ int pitch_of(int nx, int prec) {
 
 struct Layout {
     std::vector<size_t> pop_off[2];
-    size_t inst_off, tiles_off, status_off, partials_off, result_off, scratch_off, total;
+    size_t inst_off, tiles_off, status_off, partials_off, result_off, scratch_off, run_off, total;
     size_t tiles_cap, scratch_elems;
 };
 
@@ -103,6 +103,8 @@ Layout make_layout(int n, const int* nx, const int* ny, int prec) {
     L.scratch_off = off;
     L.scratch_elems = 3 * maxN;
     off = align_up(off + L.scratch_elems * sizeof(double), 256);
+    L.run_off = off;   // multi-step launches: work counter, abort flag, then one step counter per tile
+    off = align_up(off + 16 + tiles * sizeof(int), 256);
     L.total = off;
     return L;
 }
@@ -219,6 +221,12 @@ struct lbm_ctx {
     std::vector<lbm::BatchArgs<float>> bargs_f[2];
     std::vector<lbm::BatchArgs<double>> bargs_d[2];
     std::vector<int> chunk_tiles;
+    // schedule 3 (multi-step persistent launches): one argument block per chunk
+    // of up to kRunMax instances, and each chunk's first tile in the step counters
+    std::vector<lbm::RunArgs<float>> rargs_f;
+    std::vector<lbm::RunArgs<double>> rargs_d;
+    std::vector<int> run_first;
+    char* d_run = nullptr;
     int* d_status = nullptr;
     double* d_partials = nullptr;
     double* d_result = nullptr;
@@ -329,6 +337,8 @@ template <typename T> void fill_slots(const lbm_ctx* c, lbm::BatchArgs<T>& a) {
 
 // Argument blocks after a change of an instance's parameters.
 void refresh_args(lbm_ctx* c) {
+    for (auto& a : c->rargs_f)
+        for (int k = 0; k < a.n; ++k) a.phys.P[k] = c->h[a.inst[k]].pf;
     if (c->n != 1) {
         for (auto& v : c->bargs_f)
             for (auto& a : v) fill_slots(c, a);
@@ -389,6 +399,50 @@ int build_chunks(lbm_ctx* c, std::vector<lbm::BatchArgs<T>> (&out)[2], const std
     return LBM_OK;
 }
 
+// Argument blocks of the multi-step launches: instances in index order, cut
+// into chunks of up to kRunMax; a chunk steps its instances through all the
+// steps of one lbm_step call in one launch (instances are independent).
+template <typename T>
+int build_run_chunks(lbm_ctx* c, std::vector<lbm::RunArgs<T>>& out, const std::vector<int>& tx,
+                     const std::vector<int>& cnt) {
+    int* done = reinterpret_cast<int*>(c->d_run + 16);
+    int tile0 = 0;
+    for (int c0 = 0; c0 < c->n; c0 += lbm::kRunMax) {
+        const int m = std::min(lbm::kRunMax, c->n - c0);
+        lbm::RunArgs<T> a;
+        std::memset(&a, 0, sizeof a);
+        a.n = m;
+        int first = 0;
+        for (int k = 0; k < m; ++k) {
+            const int i = c0 + k;
+            const Inst& I = c->h[i];
+            a.inst[k] = i;
+            a.tiles_x[k] = tx[i];
+            a.first[k] = first;
+            first += cnt[i];
+            a.tmap[0][k] = c->maps[i].tmap[0];
+            a.tmap[1][k] = c->maps[i].tmap[1];
+            a.lat[k].pop[0] = I.pop[0];
+            a.lat[k].pop[1] = I.pop[1];
+            a.lat[k].status = I.status;
+            a.lat[k].plane = I.plane;
+            a.lat[k].nx = I.nx;
+            a.lat[k].ny = I.ny;
+            a.lat[k].pitch = I.pitch;
+            if constexpr (std::is_same<T, float>::value) a.phys.P[k] = I.pf;
+        }
+        a.first[m] = first;
+        a.ntiles = first;
+        a.done = done + tile0;
+        a.counter = reinterpret_cast<unsigned long long*>(c->d_run);
+        a.abort_flag = reinterpret_cast<int*>(c->d_run + 8);
+        c->run_first.push_back(tile0);
+        tile0 += first;
+        out.push_back(a);
+    }
+    return LBM_OK;
+}
+
 int build_tiles(lbm_ctx* c) {
     const lbm::TileCfg t = lbm::step_config(c->prec, c->cfg);
     std::vector<int> tx(c->n), cnt(c->n);
@@ -403,6 +457,11 @@ int build_tiles(lbm_ctx* c) {
     for (auto& v : c->bargs_f) v.clear();
     for (auto& v : c->bargs_d) v.clear();
     c->chunk_tiles.clear();
+    c->rargs_f.clear();
+    c->rargs_d.clear();
+    c->run_first.clear();
+    if (c->sched == 3)
+        return c->prec == LBM_FP32 ? build_run_chunks(c, c->rargs_f, tx, cnt) : build_run_chunks(c, c->rargs_d, tx, cnt);
     if (c->n == 1) return LBM_OK;   // one lattice: StepArgs, tiles from blockIdx
 
     std::vector<int> order(c->n);
@@ -423,6 +482,28 @@ int build_tiles(lbm_ctx* c) {
 // Kernel launches of one step, and their issue on a stream.
 int step_launches(const lbm_ctx* c) { return c->n == 1 ? 1 : static_cast<int>(c->chunk_tiles.size()); }
 
+// n steps of every instance as one multi-step launch per chunk (schedule 3).
+template <typename T> int run_steps_t(lbm_ctx* c, std::vector<lbm::RunArgs<T>>& chunks, int n) {
+    for (auto& a : chunks) {
+        a.nsteps = n;
+        a.parity0 = c->parity;
+        CK(c, cudaMemsetAsync(c->d_run, 0, 16, c->stream));
+        CK(c, cudaMemsetAsync(a.done, 0, static_cast<size_t>(a.ntiles) * sizeof(int), c->stream));
+        CK(c, lbm::run_launch(c->prec, c->cfg, c->d_inst, &a, c->n == 1, a.ntiles, n, kTimeoutNs, c->stream));
+    }
+    return LBM_OK;
+}
+
+int run_steps(lbm_ctx* c, int n) {
+    if (n <= 0) return LBM_OK;
+    const int rc = c->prec == LBM_FP32 ? run_steps_t(c, c->rargs_f, n) : run_steps_t(c, c->rargs_d, n);
+    if (rc) return rc;
+    c->parity ^= (n & 1);
+    c->steps += n;
+    c->launches += static_cast<long long>(c->prec == LBM_FP32 ? c->rargs_f.size() : c->rargs_d.size());
+    return LBM_OK;
+}
+
 cudaError_t launch_step(lbm_ctx* c, int parity) {
     if (c->n == 1)
         return lbm::step_launch(c->prec, c->cfg, c->d_inst, one_args(c), true, c->ntiles, parity, kTimeoutNs,
@@ -438,6 +519,8 @@ cudaError_t launch_step(lbm_ctx* c, int parity) {
 }
 
 int apply_schedule(lbm_ctx* c, int cfg, int sched) {
+    if (sched == 3 && !lbm::run_supported(c->prec, cfg))
+        return fail(c, LBM_EINVAL, "the multi-step schedule needs a tile configuration of one box per CTA%s");
     c->cfg = cfg;
     c->sched = sched;
     drop_graphs(c);
@@ -511,6 +594,7 @@ int sync_all(lbm_ctx* c) {
 }
 
 int launch_steps(lbm_ctx* c, int n) {
+    if (c->sched == 3) return run_steps(c, n);
     for (int k = 0; k < n; ++k) {
         CK(c, launch_step(c, c->parity));
         c->parity ^= 1;
@@ -728,6 +812,7 @@ int lbm_batch_create(lbm_ctx** out, int n, const int* nx, const int* ny, int pre
     c->d_partials = reinterpret_cast<double*>(c->buf + c->L.partials_off);
     c->d_result = reinterpret_cast<double*>(c->buf + c->L.result_off);
     c->d_scratch = reinterpret_cast<double*>(c->buf + c->L.scratch_off);
+    c->d_run = c->buf + c->L.run_off;
     c->h.assign(n, Inst{});
     c->maps.assign(n, Maps{});
     for (int i = 0; i < n; ++i) {
@@ -865,7 +950,7 @@ int lbm_step(lbm_ctx* c, int n) {
     int rc = ready(c);
     if (rc) return rc;
     CK(c, cudaSetDevice(c->device));
-    if (c->use_graphs && n >= kGraphSteps) {
+    if (c->use_graphs && c->sched != 3 && n >= kGraphSteps) {
         while (n >= kGraphSteps) {
             rc = ensure_graph(c, c->parity);
             if (rc) return rc;
@@ -1140,9 +1225,10 @@ int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double*
     CK(c, cudaEventCreate(&e1));
     double best = 1e300;
     int bc = c->cfg, bs = c->sched;
-    const int nsched = c->n > 1 ? lbm::kMaxSched : 1;
     for (int k = 0; k < lbm::step_config_count(c->prec); ++k)
-        for (int s = 0; s < nsched; ++s) {
+        for (int s = 0; s < lbm::kMaxSched; ++s) {
+            // one lattice: the one-step launch (0) or the multi-step one (3)
+            if ((c->n == 1 && s != 0 && s != 3) || (s == 3 && !lbm::run_supported(c->prec, k))) continue;
             rc = apply_schedule(c, k, s);
             if (rc) break;
             rc = launch_steps(c, 2);

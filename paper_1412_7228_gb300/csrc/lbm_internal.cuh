@@ -22,7 +22,7 @@
 namespace lbm {
 
 constexpr int GY = 2;          // ghost rows per side
-constexpr int kMaxSched = 3;   // CTA schedules known to lbm_set_schedule
+constexpr int kMaxSched = 4;   // CTA schedules known to lbm_set_schedule (3: multi-step persistent)
 
 template <typename T> struct Prec;
 template <> struct Prec<float> { static constexpr int GX = 8; static constexpr int HX = 4; };
@@ -120,6 +120,40 @@ template <typename T> struct BatchArgs {
     SlotLattice lat[kBatchLaunchMax];    // read by FP32 launches
     BatchPhys<T> phys;                   // FP32 only
 };
+
+// What a multi-step persistent launch needs (schedule 3): for up to
+// kRunMax instances the tensor maps of both time levels, tile counts, array
+// addresses and sizes, FP32 constants, and the launch's work counter and the
+// per-tile step counters in global memory.  Work item w is step w / ntiles
+// of tile w % ntiles (tiles in slot order, row-major within an instance); a
+// CTA takes items in that order and starts step s of a tile once every tile
+// within two nodes of it (periodic within the instance: its 3 x 3 tile
+// neighbourhood, and the tile beyond a last tile row or column one node
+// wide) has finished step s - 1.
+constexpr int kRunMax = 32;
+template <typename T> struct RunPhys {};
+template <> struct RunPhys<float> {
+    Phys<float> P[kRunMax];
+};
+template <typename T> struct RunArgs {
+    CUtensorMap tmap[2][kRunMax];        // [time level][slot]
+    int first[kRunMax + 1];              // first tile of slot k; first[n] = ntiles
+    int tiles_x[kRunMax];                // tile columns of slot k
+    int inst[kRunMax];                   // slot k -> index into the Inst array
+    int n;                               // slots in use, 1..kRunMax
+    int ntiles;                          // tiles of all slots
+    int nsteps;                          // steps this launch performs
+    int parity0;                         // time level the first step reads
+    int* done;                           // per tile: steps it has completed in this launch
+    unsigned long long* counter;         // next work item
+    int* abort_flag;                     // set when a bounded wait gave up: every CTA stops
+    SlotLattice lat[kRunMax];            // read by FP32 launches
+    RunPhys<T> phys;                     // FP32 only
+};
+
+// kernel parameters are limited to 32,764 bytes
+static_assert(sizeof(BatchArgs<float>) <= 32764 && sizeof(BatchArgs<double>) <= 32764, "argument block too large");
+static_assert(sizeof(RunArgs<float>) <= 32764 && sizeof(RunArgs<double>) <= 32764, "argument block too large");
 
 // floor(r / d) for 0 <= r < 2^31 and d >= 1 as one 64-bit multiply and a
 // shift (Granlund and Montgomery, "Division by invariant integers using
@@ -257,6 +291,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
+// Global-memory flags shared between the CTAs of one persistent launch.
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Orders this thread's earlier generic-proxy accesses (the acquire above)
+// before its later async-proxy ones (a TMA load of data other CTAs stored).
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // 3-D tiled TMA load of a box into shared memory, completing on `bar`.
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint64_t* bar) {
@@ -284,6 +333,12 @@ cudaError_t step_prepare(int prec, int k);   // sets the dynamic smem attribute
 // instances, T the context's precision.  ntiles: tiles this launch steps.
 cudaError_t step_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int parity,
                         unsigned long long timeout_ns, cudaStream_t st);
+// Multi-step persistent launch of tile configuration k (one box per CTA
+// only; false otherwise): args a RunArgs<T>, one = a single instance.  The
+// caller has zeroed the step counters, the work counter and the abort flag.
+bool run_supported(int prec, int k);
+cudaError_t run_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int nsteps,
+                       unsigned long long timeout_ns, cudaStream_t st);
 
 // Auxiliary kernels (lbm_aux.cu); `host` is the host copy of the descriptor.
 cudaError_t aux_init(const Inst& host, const Inst* d_inst, const double* rho, const double* ux,

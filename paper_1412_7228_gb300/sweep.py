@@ -76,9 +76,10 @@ def _setup(batch: L.Batch, i: int, d: Droplet, s=S_DEFAULT):
     L.Batch.init_density(batch, i, I.droplet_density(d.L, d.L, d.radius, rl, rg))
 
 
-R_OUT_GAP = 10.0   # p_out is sampled at r >= R0 + 10 (the gas beyond the interface)
+R_OUT_GAP = 10.0   # p_out is sampled at r >= R + 10 (the gas beyond the interface)
 # Laplace sampling window: the mean of Delta p (and of R_eq and the phase
-# densities) over the last WINDOW_STEPS steps, sampled every WINDOW_EVERY.
+# densities) over the last WINDOW_STEPS steps, sampled every WINDOW_EVERY
+# (each sample as in _sample).
 # A static drop keeps acoustic standing waves in the gas between it and its
 # periodic images (periods of 60-270 steps at 256^2, decaying over ~10^4
 # steps); one instant's Delta p carries them (up to 3 % of Delta p for
@@ -87,7 +88,18 @@ WINDOW_STEPS, WINDOW_EVERY = 2000, 20
 
 
 def _sample(batch: L.Batch, i: int, d: Droplet) -> Dict:
-    return batch.measure(i, d.L / 2.0, d.L / 2.0, d.radius / 2.0, d.radius + R_OUT_GAP)
+    """Laplace sampling of droplet i with discs that follow the drop's size:
+    a first pass (p_in over r <= R0/2, p_out over r >= R0 + 10) gives its
+    equimolar radius R, the second samples p_in over r <= R/2 and p_out over
+    r >= R + 10, so the inner disc stays well inside the liquid when a small
+    drop has shrunk (at 0.8 Tc an R0 = 20 drop settles at R = 12.6, and a
+    disc of radius 10 would reach into its interface)."""
+    c = d.L / 2.0
+    m = batch.measure(i, c, c, d.radius / 2.0, d.radius + R_OUT_GAP)
+    R = m["R_eq"]
+    if not (R > 0 and np.isfinite(R)):
+        return m
+    return batch.measure(i, c, c, R / 2.0, R + R_OUT_GAP)
 
 
 def _harvest(batch: L.Batch, i: int, d: Droplet, acc: Optional[List[Dict]] = None):
@@ -104,6 +116,14 @@ def _harvest(batch: L.Batch, i: int, d: Droplet, acc: Optional[List[Dict]] = Non
     d.umax = batch.stats(i)["umax"]
 
 
+def _wait():
+    """Wait for the device (no status check: unstable instances are reported
+    per instance by the caller)."""
+    import torch
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
 class Trace:
     """Per-run JSON-lines trace of the FP64 reductions (lbm_batch_stats):
     every `every` steps one line per instance with the step, the instance,
@@ -118,6 +138,7 @@ class Trace:
         self.seconds = 0.0
 
     def record(self, batch: L.Batch, step: int):
+        _wait()   # the steps so far belong to the stepping time, not to the trace
         t = time.perf_counter()
         for i in range(batch.n):
             st = batch.status(i)
@@ -183,6 +204,7 @@ def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP
         for k in range(span // every + 1):
             if k:
                 done = _advance(batch, every, done, tr)
+            _wait()   # the steps so far belong to the stepping time, not to the sampling
             t1 = time.perf_counter()
             for i, d in enumerate(droplets):
                 acc[i].append(_sample(batch, i, d))

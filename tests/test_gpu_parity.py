@@ -99,9 +99,38 @@ def test_every_tile_config_and_graphs_are_bit_identical(P):
     rho0 = I.droplet_density(90, 75, 20, rl, rg)
     for prec in (P.LBM_FP64, P.LBM_FP32):
         base = gpu_run(P, prec, eos, op, rho0, 70, rho_ref=rg, cfg=0)
-        for k in range(len(P.lbm_tile_configs(prec))):
+        for k, c in enumerate(P.lbm_tile_configs(prec)):
             assert np.array_equal(gpu_run(P, prec, eos, op, rho0, 70, rho_ref=rg, cfg=k), base), (prec, k)
+            if c[3] == 1:   # the multi-step persistent launch of the same tiles
+                assert np.array_equal(gpu_run(P, prec, eos, op, rho0, 70, rho_ref=rg, cfg=k, sched=3), base), \
+                    (prec, k, 3)
         assert np.array_equal(gpu_run(P, prec, eos, op, rho0, 70, rho_ref=rg, graphs=True), base)
+
+
+def test_multi_step_launch_in_pieces_and_tiny_lattices(P):
+    """The multi-step schedule gives the one-step bits however the steps are
+    split into calls (odd counts flip the time level inside a launch), on a
+    lattice of a single tile (the tile is its own periodic neighbourhood) and
+    on ones whose tiles do not divide them, and on one whose last tile column
+    and row are one node wide (the tiles on either side of them depend on each
+    other), with graphs requested (not used)."""
+    eos, op, rg, rl = cs_case(P)
+    for nx, ny in ((64, 16), (90, 75), (200, 37), (257, 49), (20, 49)):
+        rho0 = I.droplet_density(nx, ny, min(nx, ny) / 4, rl, rg)
+        for prec in (P.LBM_FP64, P.LBM_FP32):
+            base = gpu_run(P, prec, eos, op, rho0, 37, rho_ref=rg)
+            lat = P.Lattice(nx, ny, prec)
+            lat.set_schedule(0, 3)
+            lat.set_params(eos, op.A, op.kappa, G=op.G, s=op.s, rho_ref=rg)
+            lat.init_density(rho0)
+            lat.use_graphs(True)
+            n0 = lat.kernel_launches
+            for n in (1, 0, 7, 29):
+                lat.step(n)
+            assert lat.kernel_launches - n0 == 3 and lat.steps_done == 37
+            lat.sync()
+            assert np.array_equal(lat.read_populations(), base), (nx, ny, prec)
+            lat.close()
 
 
 def test_vdw_flat_interface_matches_oracle_and_table1(P, golden):
@@ -194,7 +223,7 @@ def test_batch_equals_separate_runs(P):
     rhos = [I.droplet_density(nx, ny, min(nx, ny) / 4, rl, rg) for nx, ny in shapes]
     for prec in (P.LBM_FP64, P.LBM_FP32):
         solo = [gpu_run(P, prec, eos, op, r, 40, rho_ref=rg) for r in rhos]
-        for sched in (0, 1, 2):
+        for sched in (0, 1, 2, 3):
             b = P.Batch([s[0] for s in shapes], [s[1] for s in shapes], prec)
             b.set_schedule(0, sched)
             for i, r in enumerate(rhos):
@@ -211,7 +240,8 @@ def test_batch_of_more_than_64_instances(P):
     """A batch beyond one launch's 64 instances (70 uneven lattices: two
     launches per step) gives every instance the bits it gets alone, for each
     CTA schedule, in the one-tile-per-CTA and the persistent tile shapes, with
-    CUDA graphs, and counts two kernel launches per step."""
+    CUDA graphs, and counts two kernel launches per step (the multi-step
+    schedule: one launch per 32 instances for all the steps)."""
     eos, op, rg, rl = cs_case(P)
     rng = np.random.default_rng(70)
     shapes = [(int(rng.integers(16, 48)), int(rng.integers(24, 56))) for _ in range(70)]
@@ -219,21 +249,21 @@ def test_batch_of_more_than_64_instances(P):
     steps = 40
     solo = [gpu_run(P, P.LBM_FP32, eos, op, r, steps, rho_ref=rg) for r in rhos]
     persistent = [k for k, c in enumerate(P.lbm_tile_configs(P.LBM_FP32)) if c[3] == 2]
-    for cfg in (0, persistent[0]):
-        for sched in (0, 1, 2):
-            b = P.Batch([s[0] for s in shapes], [s[1] for s in shapes], P.LBM_FP32)
-            b.set_schedule(cfg, sched)
-            for i, r in enumerate(rhos):
-                b.set_params(i, eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
-                b.init_density(i, r)
-            b.use_graphs(True)
-            n0 = b.kernel_launches
-            b.step(steps)
-            assert b.kernel_launches - n0 == 2 * steps
-            outs = [b.read_populations(i) for i in range(len(shapes))]
-            b.close()
-            for i in range(len(shapes)):
-                assert np.array_equal(outs[i], solo[i]), (cfg, sched, i)
+    for cfg, sched in [(c, s) for c in (0, persistent[0]) for s in (0, 1, 2)] + [(0, 3)]:
+        b = P.Batch([s[0] for s in shapes], [s[1] for s in shapes], P.LBM_FP32)
+        b.set_schedule(cfg, sched)
+        for i, r in enumerate(rhos):
+            b.set_params(i, eos, op.A, op.kappa, s=S_CFG, rho_ref=rg)
+            b.init_density(i, r)
+        b.use_graphs(True)
+        n0 = b.kernel_launches
+        b.step(steps)
+        # one launch per step and 64 instances; the multi-step schedule one launch per 32
+        assert b.kernel_launches - n0 == (3 if sched == 3 else 2 * steps)
+        outs = [b.read_populations(i) for i in range(len(shapes))]
+        b.close()
+        for i in range(len(shapes)):
+            assert np.array_equal(outs[i], solo[i]), (cfg, sched, i)
 
 
 def test_checkpoint_resume_is_bit_identical(P, tmp_path):
@@ -297,15 +327,19 @@ def test_nan_initial_field_is_rejected(P):
     lat.close()
 
 
-def test_bounded_wait_reports_timeout_and_context_survives(P):
+@pytest.mark.parametrize("sched", [0, 3])
+def test_bounded_wait_reports_timeout_and_context_survives(P, sched):
     """A barrier phase nothing completes: every CTA gives up after its
-    limit, the status reads ETIMEOUT, and the context keeps working."""
+    limit, the status reads ETIMEOUT, and the context keeps working (in the
+    multi-step launch the CTA that gives up raises the launch's abort flag
+    and the other CTAs stop at their next work item)."""
     eos, op, rg, rl = cs_case(P)
     rho0 = I.droplet_density(64, 32, 8, rl, rg)
     lat = P.Lattice(64, 32, P.LBM_FP32)
+    lat.set_schedule(0, sched)
     lat.set_params(eos, op.A, op.kappa, s=S_CFG, rho_ref=rg, flags=P.LBM_FLAG_TEST_FORCE_TIMEOUT)
     lat.init_density(rho0)
-    lat.step(1)
+    lat.step(1 if sched == 0 else 5)
     with pytest.raises(P.LbmError) as ei:
         lat.sync()
     assert ei.value.code == -5

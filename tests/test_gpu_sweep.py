@@ -24,6 +24,16 @@ def SW():
     return sweep
 
 
+def oracle_sample(p, f, N, R0, gap=10.0):
+    """The sweep's Laplace sampling on the oracle: a first pass with discs
+    from R0 gives the equimolar radius R, the second samples r <= R/2 and
+    r >= R + gap."""
+    rho = O.macro(p, f)[0]
+    d = An.pressure_jump(p, rho, N / 2, N / 2, R0 / 2, R0 + gap)
+    R = d["R_eq"]
+    return An.pressure_jump(p, rho, N / 2, N / 2, R / 2, R + gap) if R > 0 else d
+
+
 def oracle_laplace(kappa, radii, N, steps, tr=0.7, A=-0.85, gap=10.0, window=(2000, 20)):
     """The oracle's sigma with the sweep's sampling: Delta p and R_eq are the
     means over the last window[0] steps, one sample every window[1]."""
@@ -40,7 +50,7 @@ def oracle_laplace(kappa, radii, N, steps, tr=0.7, A=-0.85, gap=10.0, window=(20
         for k in range(span // every + 1):
             if k:
                 O.step(p, f, every)
-            samples.append(An.pressure_jump(p, O.macro(p, f)[0], N / 2, N / 2, R / 2, R + gap))
+            samples.append(oracle_sample(p, f, N, R, gap))
         dps.append(np.mean([d["dp"] for d in samples]))
         Rs.append(np.mean([d["R_eq"] for d in samples]))
     return An.laplace_fit(dps, Rs)

@@ -229,3 +229,27 @@ def test_density_dependent_viscosity_sets_the_shear_decay(rho0, nu_expect):
     k = 2 * math.pi / L
     nu_meas = -math.log(a2 / a1) / (k * k * 300)
     assert abs(nu_meas / nu_expect - 1) < 3e-3
+
+
+def test_threaded_build_gives_the_same_bits():
+    """The OpenMP build of the oracle (nodes shared among threads) computes
+    every node as the serial build does: same bits after 40 steps of a
+    droplet, also with the test-only walls and a body force."""
+    import lbm_inputs as I
+    from oracle import analysis as An
+    base = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, A=-0.85, kappa=0.3)
+    _, Tc, _ = An.critical_point(base)
+    p = An.with_T(base, 0.7 * Tc)
+    rg, rl, _ = An.maxwell(p)
+    rho0 = I.droplet_density(70, 46, 12, rl, rg)
+    f1 = O.init_equilibrium(rho0)
+    f4 = f1.copy()
+    O.step(p, f1, 40)
+    O.step(p, f4, 40, threads=4)
+    assert np.array_equal(f1, f4)
+    w = O.Params(G=0.0, walls_y=True, fext_x=1e-5, s=[1.0] * 9)
+    g1 = O.init_equilibrium(np.ones((12, 9)))
+    g4 = g1.copy()
+    O.step(w, g1, 30)
+    O.step(w, g4, 30, threads=3)
+    assert np.array_equal(g1, g4)
