@@ -85,13 +85,14 @@ def measured_peak():
         return PEAK_FALLBACK_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("lbm_step.cu", "lbm_internal.cuh")
+KERNEL_SOURCES = ("lbm_step_kernels.cuh", "lbm_step_f32.cu", "lbm_step_f64.cu", "lbm_step.cu", "lbm_internal.cuh")
 
 
 def kernel_sources_sha():
-    """First 16 hex digits of the SHA-256 of the step kernel's sources (the
-    kernel file followed by the header it compiles), the key under which a
-    committed ncu figure is valid."""
+    """First 16 hex digits of the SHA-256 of the step kernels' sources (the
+    kernel header, the two translation units that instantiate it, the
+    dispatch file and the header they all compile, in that order), the key
+    under which a committed ncu figure is valid."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", name), "rb") as fh:
@@ -276,6 +277,19 @@ def plain_method_64(torch, P, steps=10000):
         out[name] = {"seconds": t, "us_per_step": t / steps * 1e6, "mlups": 64 * 64 * steps / t / 1e6,
                      "tile": list(P.lbm_tile_configs(prec)[k])}
     return out
+
+
+def laplace_sweep_fp32():
+    """The Laplace-law sweep at its full size in FP32: 60 droplets of 256^2
+    (R0 = 20..60, kappa 0 / 0.1 / 0.3 / 0.5, T = 0.6 / 0.7 / 0.8 Tc), 3x10^4
+    steps, autotuned batched launches, Laplace sampling averaged over the
+    last 2000 steps; sigma from Delta p against 1/R_eq per (T, kappa)."""
+    from paper_1412_7228_gb300 import sweep as SW
+    fits, info = SW.laplace_sweep()
+    return {"workload": "60 droplets of 256^2, 3x10^4 steps, FP32", "stepping_seconds": info["seconds"],
+            "mlups": info["mlups"], "tile": list(info["tune"][:2]) if info.get("tune") else None,
+            "fits": [{"t_over_tc": f.t_over_tc, "kappa": f.kappa, "sigma": f.sigma, "r2": f.r2, "drops": len(f.radii)}
+                     for f in fits]}
 
 
 def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
@@ -599,6 +613,11 @@ def run_ours(args):
     if not args.no_workloads:
         plain = plain_method_64(torch, P)
 
+    # ---- the Laplace-law sweep, FP32, at its full size ----------------------
+    laplace = None
+    if not args.no_sweep:
+        laplace = laplace_sweep_fp32()
+
     # ---- batched uneven sweep against the same lattices one after another ---
     batched = None
     if not args.no_sweep:
@@ -631,7 +650,7 @@ def run_ours(args):
                 {"tile": list(tile), "parallelism": "replicas" if ws > 1 else "single"}, **graph_use(args.steps))),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "fp64": fp64, "other_workloads": others, "plain_method_64x64": plain,
-            "batched_sweep": batched,
+            "laplace_sweep": laplace, "batched_sweep": batched,
             "status_ok": status_ok,
         }
         print(json.dumps(line), flush=True)

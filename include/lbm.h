@@ -167,15 +167,20 @@ int lbm_batch_set_viscosity(lbm_ctx* ctx, int i, int enable, double nu_gas, doub
 
 /* Initial state f_a = M^-1 m_eq(rho, u) (Eq. 4) from host fields of nx*ny
  * doubles; ux, uy may be NULL (zero velocity).  Resets the step counter and
- * the instance's status. */
+ * the instance's status.  The fields are copied to the device and checked
+ * there first: a density that is not finite, positive and below the EOS's
+ * upper limit (4/b Carnahan-Starling, 1/b otherwise; any positive density
+ * when G = 0) or a velocity that is not finite returns LBM_EINVAL and leaves
+ * the instance as it was.  Synchronous. */
 int lbm_init_density(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
 int lbm_batch_init_density(lbm_ctx* ctx, int i, const double* rho, const double* ux,
                            const double* uy);
 
 /* Enqueue n time steps (Eqs. 1, 9, 10, 23, 25, 26: density and psi, hybrid
  * force, modifying tensor, moment-space collision, streaming) of every
- * instance; one fused kernel launch per step, replayed from a CUDA graph
- * when graphs are on.  Asynchronous. */
+ * instance: one fused kernel launch per step (and per 64 instances),
+ * replayed from a CUDA graph when graphs are on, or with schedule 3 one
+ * launch per call (and per 32 instances).  Asynchronous. */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* Wait for the stream; return the first sticky status of any instance. */

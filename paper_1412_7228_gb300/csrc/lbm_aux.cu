@@ -47,6 +47,22 @@ __global__ void k_init(const Inst* __restrict__ I, const double* __restrict__ rh
     }
 }
 
+// The checks of an initial field, on the device: bit 1 of *bad when a
+// density is not finite, not positive or not below rho_max, bit 2 when a
+// velocity is not finite (the caller has zeroed *bad).
+__global__ void k_check_init(const double* __restrict__ rho, const double* __restrict__ ux,
+                             const double* __restrict__ uy, long long N, double rho_max, int* bad) {
+    int b = 0;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double r = rho[i];
+        if (!(r > 0.0) || !(r < rho_max) || !isfinite(r)) b |= 1;
+        if ((ux && !isfinite(ux[i])) || (uy && !isfinite(uy[i]))) b |= 2;
+    }
+    b = __reduce_or_sync(0xffffffffu, b);
+    if (b && (threadIdx.x & 31) == 0) atomicOr(bad, b);
+}
+
 // Ghost cells x in [-2,0) U [nx,nx+2), y in [-2,0) U [ny,ny+2) of every plane.
 template <typename T> __global__ void k_ghosts(const Inst* __restrict__ I, int parity) {
     const int nx = I->nx, ny = I->ny;
@@ -353,6 +369,12 @@ cudaError_t aux_init(const Inst& h, const Inst* d, const double* rho, const doub
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return aux_fill_ghosts(h, d, parity, st);
+}
+
+cudaError_t aux_check_init(const double* rho, const double* ux, const double* uy, long long N, double rho_max,
+                           int* bad, cudaStream_t st) {
+    k_check_init<<<grid_for(N), kThreads, 0, st>>>(rho, ux, uy, N, rho_max, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t aux_fill_ghosts(const Inst& h, const Inst* d, int parity, cudaStream_t st) {

@@ -21,6 +21,9 @@ using lbm::Inst;
 namespace {
 
 constexpr unsigned long long kTimeoutNs = 1000000000ull;   // bounded TMA wait: 1 s
+#ifndef LBM_RUN_CHUNK_MB
+#define LBM_RUN_CHUNK_MB 64   // populations per multi-step launch, MiB (see build_run_chunks)
+#endif
 
 // An NVTX range over the enclosing scope (host side: it brackets the calls
 // that enqueue or wait for the work); a no-op unless a profiler is attached.
@@ -400,15 +403,24 @@ int build_chunks(lbm_ctx* c, std::vector<lbm::BatchArgs<T>> (&out)[2], const std
 }
 
 // Argument blocks of the multi-step launches: instances in index order, cut
-// into chunks of up to kRunMax; a chunk steps its instances through all the
-// steps of one lbm_step call in one launch (instances are independent).
+// into chunks of up to kRunMax instances whose populations (both time
+// levels) take at most kRunChunkBytes, unless one instance alone takes more;
+// a chunk steps its instances through all the steps of one lbm_step call in
+// one launch (instances are independent), so a chunk that fits in L2 (129 MB
+// on GB300) keeps its populations there from step to step.
+constexpr size_t kRunChunkBytes = static_cast<size_t>(LBM_RUN_CHUNK_MB) << 20;
 template <typename T>
 int build_run_chunks(lbm_ctx* c, std::vector<lbm::RunArgs<T>>& out, const std::vector<int>& tx,
                      const std::vector<int>& cnt) {
     int* done = reinterpret_cast<int*>(c->d_run + 16);
     int tile0 = 0;
-    for (int c0 = 0; c0 < c->n; c0 += lbm::kRunMax) {
-        const int m = std::min(lbm::kRunMax, c->n - c0);
+    for (int c0 = 0, m = 0; c0 < c->n; c0 += m) {
+        size_t bytes = 0;
+        for (m = 0; c0 + m < c->n && m < lbm::kRunMax; ++m) {
+            const size_t b = 2 * 9 * static_cast<size_t>(c->h[c0 + m].plane) * c->esz;
+            if (m > 0 && bytes + b > kRunChunkBytes) break;
+            bytes += b;
+        }
         lbm::RunArgs<T> a;
         std::memset(&a, 0, sizeof a);
         a.n = m;
@@ -918,12 +930,6 @@ int lbm_batch_init_density(lbm_ctx* c, int i, const double* rho, const double* u
     const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
     // the EOS range only matters when psi is evaluated (G != 0)
     const double rmax = c->hp[i].G != 0.0 ? eos_rho_max(c->hp[i].eos) : HUGE_VAL;
-    for (size_t k = 0; k < N; ++k) {
-        if (!(rho[k] > 0.0) || !(rho[k] < rmax) || !std::isfinite(rho[k]))
-            return fail(c, LBM_EINVAL, "initial density must be finite, positive and inside the EOS range%s");
-        if ((ux && !std::isfinite(ux[k])) || (uy && !std::isfinite(uy[k])))
-            return fail(c, LBM_EINVAL, "initial velocity must be finite%s");
-    }
     CK(c, cudaSetDevice(c->device));
     CK(c, cudaStreamSynchronize(c->stream));
     double* d_rho = c->d_scratch;
@@ -932,6 +938,15 @@ int lbm_batch_init_density(lbm_ctx* c, int i, const double* rho, const double* u
     CK(c, cudaMemcpyAsync(d_rho, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (ux) CK(c, cudaMemcpyAsync(d_ux, ux, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (uy) CK(c, cudaMemcpyAsync(d_uy, uy, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // the field is checked on the device before anything of the instance is written
+    int* d_bad = reinterpret_cast<int*>(c->d_result);
+    int bad = 0;
+    CK(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+    CK(c, lbm::aux_check_init(d_rho, d_ux, d_uy, static_cast<long long>(N), rmax, d_bad, c->stream));
+    CK(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (bad & 1) return fail(c, LBM_EINVAL, "initial density must be finite, positive and inside the EOS range%s");
+    if (bad & 2) return fail(c, LBM_EINVAL, "initial velocity must be finite%s");
     CK(c, lbm::aux_init(c->h[i], c->d_inst + i, d_rho, d_ux, d_uy, c->parity, c->stream));
     CK(c, cudaMemsetAsync(c->d_status + i, 0, sizeof(int), c->stream));
     CK(c, cudaStreamSynchronize(c->stream));

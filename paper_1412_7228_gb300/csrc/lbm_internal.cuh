@@ -344,6 +344,9 @@ cudaError_t run_launch(int prec, int k, const Inst* d_insts, const void* args, b
 cudaError_t aux_init(const Inst& host, const Inst* d_inst, const double* rho, const double* ux,
                      const double* uy, int parity, cudaStream_t st);
 cudaError_t aux_fill_ghosts(const Inst& host, const Inst* d_inst, int parity, cudaStream_t st);
+// bad |= 1: a density not finite, positive and below rho_max; |= 2: a velocity not finite
+cudaError_t aux_check_init(const double* rho, const double* ux, const double* uy, long long N, double rho_max,
+                           int* bad, cudaStream_t st);
 cudaError_t aux_gather_plane(const Inst& host, const Inst* d_inst, int parity, int a, double* out,
                              cudaStream_t st);
 // field: 0 rho, 1 ux, 2 uy, 3 psi

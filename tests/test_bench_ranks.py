@@ -69,7 +69,7 @@ def test_traffic_figure_is_used_only_for_the_profiled_kernel():
     sys.path.insert(0, ROOT)
     import bench
     h = hashlib.sha256()
-    for name in ("lbm_step.cu", "lbm_internal.cuh"):
+    for name in ("lbm_step_kernels.cuh", "lbm_step_f32.cu", "lbm_step_f64.cu", "lbm_step.cu", "lbm_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1412_7228_gb300", "csrc", name), "rb").read())
     sha = h.hexdigest()[:16]
     assert bench.kernel_sources_sha() == sha
