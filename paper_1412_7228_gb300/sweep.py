@@ -187,7 +187,9 @@ def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP
     if schedule is not None:
         batch.set_schedule(*schedule)
     elif autotune:
-        tune = batch.autotune(5)
+        # enough steps that the multi-step schedule's launch is measured over
+        # many steps, as a long sweep runs it
+        tune = batch.autotune(40)
     if graphs:
         batch.use_graphs(True)
     acc = None
