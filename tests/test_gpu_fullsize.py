@@ -109,12 +109,14 @@ def test_bench_configuration_conserves_mass(setup):
     assert abs(st["mom_x"]) < 1e-6 * m0 and abs(st["mom_y"]) < 1e-6 * m0
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 1e-14)])
-def test_batched_sweep_configuration_matches_oracle_on_sampled_windows(setup, prec, tol):
+@pytest.mark.parametrize("prec,tol,sched", [(1, 2e-6, None), (2, 1e-14, None), (1, 2e-6, 3)])
+def test_batched_sweep_configuration_matches_oracle_on_sampled_windows(setup, prec, tol, sched):
     """The 64 uneven droplets of the batched sweep (L in {128, ..., 1024},
     seed 7228) in one batched launch, tile shape autotuned and graphs on
-    as the sweep runs them: 3 steps, then three oracle windows per instance
-    (on the interface, across the wrapped corner, at a seeded place).
+    as the sweep runs them (or in the multi-step schedule: one launch per
+    chunk of at most 32 instances and 64 MiB of populations): 3 steps, then three oracle
+    windows per instance (on the interface, across the wrapped corner, at a
+    seeded place).
     Error: max |rho - rho_oracle| over a window / max rho_oracle there.  A
     gas node next to the interface receives populations of liquid size, so
     its error scales with the liquid density, not its own: in FP32 (unit
@@ -132,7 +134,10 @@ def test_batched_sweep_configuration_matches_oracle_on_sampled_windows(setup, pr
         b.init_density(i, rho0)
         op = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, T=eos.T, A=d.A, kappa=d.kappa, s=list(S_CFG))
         cases.append((d, op, rho0))
-    b.autotune(3)
+    if sched is None:
+        b.autotune(3)
+    else:
+        b.set_schedule(0, sched)
     b.use_graphs(True)
     b.step(STEPS)
     rng = np.random.default_rng(7228)
