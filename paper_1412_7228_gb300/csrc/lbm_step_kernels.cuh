@@ -208,20 +208,21 @@ template <int EOSK, typename T> __device__ __forceinline__ T radicand_step(const
     return P.two_over_G * fma(rho, T(-1.0 / 3.0), p);
 }
 
-// psi of Eq. 10 for the Carnahan-Starling law in FP64, with the division by
-// q^3 = (1 - b rho/4)^3 and the square root folded into one reciprocal
-// square root: with W = (2/G) rho [K R T num - (K a rho + 1/3) q^3] (num the
-// law's numerator polynomial), psi^2 = W / q^3, so psi = W / sqrt(W q^3).
-// 1/(2 sqrt(x)) comes from the hardware estimate refined by two Goldschmidt
-// steps, as in Fast<double>::sqrt.  kR = (2/G) K R T, kA = (2/G) K a,
-// k3 = (2/G)/3.  A negative radicand gives NaN (as the square root does),
-// psi(W = 0) = 0.
-__device__ __forceinline__ double psi_cs_fp64(double b4, double kR, double kA, double k3, double rho) {
-    const double n = b4 * rho, q = 1.0 - n;
-    const double num = fma(n, fma(n, 1.0 - n, 1.0), 1.0);
-    const double q3 = q * q * q;
-    const double W = rho * fma(-fma(kA, rho, k3), q3, kR * num);
-    const double x = W * q3;
+// psi of Eq. 10 in FP64 with the law's division(s) and the square root
+// folded into one reciprocal square root.  Each law's radicand
+// (2/G)(p_EOS - rho/3) is written as W / D with D > 0 inside the law's range:
+//   Carnahan-Starling  D = q^3, q = 1 - b rho/4,  W = rho [kR num - (kA rho + k3) q^3]
+//                      (num = 1 + n + n^2 - n^3, n = b rho/4);
+//   van der Waals      D = d, d = 1 - b rho,       W = rho [kR - (kA rho + k3) d];
+//   Peng-Robinson      D = d e, e = 1 + 2 b rho - (b rho)^2,
+//                      W = rho [kR e - (kAa rho + k3 e) d];
+// with kR = (2/G) K R T, kA = (2/G) K a, kAa = (2/G) K a alpha(T),
+// k3 = (2/G)/3.  Then psi = W / sqrt(W D); 1/(2 sqrt(x)) comes from the
+// hardware estimate refined by two Goldschmidt steps, as in
+// Fast<double>::sqrt.  A negative radicand gives NaN (as the square root
+// does), psi(W = 0) = 0.
+__device__ __forceinline__ double psi_fold_fp64(double W, double D) {
+    const double x = W * D;
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     const double g0 = x * y, h0 = 0.5 * y;
@@ -230,6 +231,22 @@ __device__ __forceinline__ double psi_cs_fp64(double b4, double kR, double kA, d
     const double r1 = fma(-g1, h1, 0.5);
     const double h2 = fma(h1, r1, h1);
     return W == 0.0 ? 0.0 : (W + W) * h2;
+}
+
+template <int EOSK>
+__device__ __forceinline__ double psi_fp64(const EosRegs<double>& E, double kR, double kA, double kAa, double k3,
+                                           double rho) {
+    const int eos = EOSK ? EOSK : E.eos;
+    if (eos == LBM_EOS_CS) {
+        const double n = E.b4 * rho, q = 1.0 - n;
+        const double num = fma(n, fma(n, 1.0 - n, 1.0), 1.0);
+        const double q3 = q * q * q;
+        return psi_fold_fp64(rho * fma(-fma(kA, rho, k3), q3, kR * num), q3);
+    }
+    const double br = E.b * rho, d = 1.0 - br;
+    if (eos == LBM_EOS_VDW) return psi_fold_fp64(rho * fma(-fma(kA, rho, k3), d, kR), d);
+    const double e = fma(br, 2.0 - br, 1.0);
+    return psi_fold_fp64(rho * fma(-fma(kAa, rho, k3 * e), d, kR * e), d * e);
 }
 
 // Hybrid force (Eq. 9) and modifying tensor (Eq. 23, x G/2) of one node
@@ -286,10 +303,10 @@ template <typename Gm, int EOSK, typename T>
 __device__ __forceinline__ void psi_ring(const T* sf, T* sp, const EosRegs<T>& E, T rho_ref, int tid, int tx,
                                          int ty) {
     constexpr int BX = Gm::BX;
-    // FP64 Carnahan-Starling: psi_cs_fp64 on every path (the law fixed at
-    // compile time or read at run time), so that every tile computes the same bits
-    const bool cs64 = sizeof(T) == 8 && (EOSK ? EOSK : E.eos) == LBM_EOS_CS;
-    const T kR = E.two_over_G * E.K * E.RT, kA = E.two_over_G * E.K * E.a, k3 = E.two_over_G * T(1.0 / 3.0);
+    // FP64: psi_fp64 on every path (the law fixed at compile time or read at
+    // run time), so that every tile computes the same bits
+    const T kR = E.two_over_G * E.K * E.RT, kA = E.two_over_G * E.K * E.a, kAa = E.two_over_G * E.K * E.aalpha;
+    const T k3 = E.two_over_G * T(1.0 / 3.0);
     auto ring = [&](int i, int j) {
         const T* q = sf + (j + 1) * Gm::WB + (i + Gm::HX - 1);
         T g[9];
@@ -298,8 +315,7 @@ __device__ __forceinline__ void psi_ring(const T* sf, T* sp, const EosRegs<T>& E
         const T rho = rho_ref + rho_dev(g);
         T psi;
         if constexpr (sizeof(T) == 8) {
-            if (cs64) psi = psi_cs_fp64(E.b4, kR, kA, k3, rho);
-            else psi = Fast<T>::sqrt(radicand_step<EOSK>(E, rho));
+            psi = psi_fp64<EOSK>(E, kR, kA, kAa, k3, rho);
         } else {
             psi = Fast<T>::sqrt(radicand_step<EOSK>(E, rho));
         }
@@ -788,14 +804,13 @@ __device__ __forceinline__ void run_body(const Inst* __restrict__ insts, unsigne
                                               tx, ty);
         if (bad) atomicOr(status, ST_UNSTABLE);
         __syncthreads();   // every store of the tile, and every read of its box, is done
-        // warp 1 publishes the tile's step (its fence waits for the CTA's stores
-        // to reach the GPU scope) while warp 0 already finds the next item and
-        // issues its load; warp 0 never waits for warp 1 except through the step
-        // counter, so an item that depends on this one simply waits a little longer
-        if (tid == 32) {
-            __threadfence();
-            st_release_gpu(a.done + t, s + 1);
-        }
+        // warp 1 publishes the tile's step while warp 0 already finds the next
+        // item and issues its load; warp 0 never waits for warp 1 except through
+        // the step counter, so an item that depends on this one simply waits a
+        // little longer.  The release store is cumulative: the barrier above
+        // orders every thread's stores of the tile before it, so a CTA that
+        // acquires the counter sees them all
+        if (tid == 32) st_release_gpu(a.done + t, s + 1);
     }
 }
 
