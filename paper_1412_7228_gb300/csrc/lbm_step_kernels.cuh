@@ -904,7 +904,10 @@ template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
             return cudaSuccess;
         }
     }
-    // every CTA of the grid resident (cooperative launch), no more CTAs than work items
+    // every CTA of the grid resident (cooperative launch), no more CTAs than
+    // work items, and no more than two per tile: beyond that the extra CTAs of
+    // a small lattice would only wait for steps their neighbours have not
+    // finished, and hold SM slots that other launches could use
     static cudaError_t run(const Inst* d, const void* args, bool one, int ntiles, int nsteps, unsigned long long to,
                            cudaStream_t st) {
         if constexpr (NBUF != 1) {
@@ -913,8 +916,10 @@ template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
             const long long items = static_cast<long long>(ntiles) * nsteps;
             const int cap = run_cap[one ? 1 : 0];
             if (cap < 1) return cudaErrorNotSupported;
+            long long grid = items < cap ? items : cap;
+            if (grid > 2ll * ntiles) grid = 2ll * ntiles;
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(static_cast<unsigned>(items < cap ? items : cap));
+            cfg.gridDim = dim3(static_cast<unsigned>(grid));
             cfg.blockDim = dim3(NT);
             cfg.dynamicSmemBytes = Gm::smem;
             cfg.stream = st;
