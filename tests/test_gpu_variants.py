@@ -24,9 +24,11 @@ def P():
     return P
 
 
-def _run(P, prec, eos, op, rho0, steps, rho_ref, visc=None):
+def _run(P, prec, eos, op, rho0, steps, rho_ref, visc=None, sched=0, tile=0):
     ny, nx = rho0.shape
     lat = P.Lattice(nx, ny, prec)
+    if sched or tile:
+        lat.set_schedule(tile, sched)
     lat.set_params(eos, op.A, op.kappa, G=op.G, s=op.s, rho_ref=rho_ref, flags=P.LBM_FLAG_LI_EPS if op.li_eps else 0)
     if visc:
         lat.set_viscosity(*visc)
@@ -112,3 +114,31 @@ def test_bgk_limit_equal_rates(P):
     f = O.init_equilibrium(rho0)
     O.step(op, f, 40)
     assert _rel(_run(P, P.LBM_FP64, eos, op, rho0, 40, 0.0095), f) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_every_variant_gives_the_same_bits_in_every_schedule(P, prec):
+    """The variants take the general path or other pressure laws in the
+    fused kernels: the Peng-Robinson and van der Waals laws, the
+    density-dependent viscosity, Li's source entry and G = 0.  One step per
+    launch and the multi-step schedule, on a tile shape that does not divide
+    the lattice, give the same bits for each."""
+    from paper_1412_7228_gb300 import experiments as E
+    eos_pr, op_pr = _pr(P)
+    vdw = E.vdw_eos(0.9, 0.3)
+    op_vdw = O.Params(eos=O.EOS_VDW, a=vdw.a, b=vdw.b, R=1.0, K=0.3, T=vdw.T, A=-0.5, kappa=0.5, s=[1.0] * 9)
+    eos_v, op_v = _pr(P, kappa=-1.0)
+    cs = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, T=0.066)
+    op_li = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, T=0.066, A=-0.85, kappa=0.5, li_eps=True)
+    op_g0 = O.Params(eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0, T=0.066, A=-0.85, kappa=0.5, G=0.0)
+    cases = [
+        (eos_pr, op_pr, I.droplet_density(150, 70, 18, 7.17, 0.0372, width=4.0), 0.0372, None),
+        (vdw, op_vdw, I.slab_density(150, 70, 5.8, 1.47, width=4.0), 1.47, None),
+        (eos_v, op_v, I.ellipse_density(150, 70, 30, 20, 7.17, 0.0167, width=4.0), 0.0167, (0.2, 0.05, 0.0167, 7.17)),
+        (cs, op_li, I.droplet_density(150, 70, 14, 0.36, 0.0095), 0.0095, None),
+        (cs, op_g0, 0.3 + 0.01 * I.droplet_density(150, 70, 14, 1.0, 0.0), 0.3, None),
+    ]
+    for eos, op, rho0, rho_ref, visc in cases:
+        base = _run(P, prec, eos, op, rho0, 23, rho_ref, visc)
+        assert np.all(np.isfinite(base))
+        assert np.array_equal(_run(P, prec, eos, op, rho0, 23, rho_ref, visc, sched=3), base), (op.eos, visc)
