@@ -268,9 +268,9 @@ def plain_method_64(torch, P, steps=10000):
         lat = P.Lattice(64, 64, prec)
         lat.set_params(eos, A_CFG, 0.0, G=-1.0, s=S_CFG, rho_ref=rg)
         lat.init_density(rho0)
+        lat.use_graphs(True)
         k, sch, _ = lat.autotune(40)
         lat.init_density(rho0)
-        lat.use_graphs(True)
         t = time_steps(torch, lat, steps)
         lat.sync()
         lat.close()
@@ -308,8 +308,8 @@ def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
     b = P.Batch([d.L for d in drops], [d.L for d in drops], P.LBM_FP32, stream=st)
     for i, d in enumerate(drops):
         SW._setup(b, i, d)
-    tile, sched, _ = b.autotune(40)
     b.use_graphs(True)
+    tile, sched, _ = b.autotune(40)
     b.step(64)
     b.sync()
     t_b = time_steps(torch, b, steps)
@@ -322,8 +322,8 @@ def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
     for d in drops:
         lat = P.Lattice(d.L, d.L, P.LBM_FP32, stream=st)
         SW._setup(lat, 0, d)
-        lat.autotune(40)
         lat.use_graphs(True)
+        lat.autotune(40)
         lat.step(64)
         lats.append(lat)
     torch.cuda.synchronize()

@@ -531,8 +531,6 @@ cudaError_t launch_step(lbm_ctx* c, int parity) {
 }
 
 int apply_schedule(lbm_ctx* c, int cfg, int sched) {
-    if (sched == 3 && !lbm::run_supported(c->prec, cfg))
-        return fail(c, LBM_EINVAL, "the multi-step schedule needs a tile configuration of one box per CTA%s");
     c->cfg = cfg;
     c->sched = sched;
     drop_graphs(c);
@@ -959,15 +957,12 @@ int lbm_init_density(lbm_ctx* c, const double* rho, const double* ux, const doub
     return lbm_batch_init_density(c, 0, rho, ux, uy);
 }
 
-int lbm_step(lbm_ctx* c, int n) {
-    if (!c || n < 0) return LBM_EINVAL;
-    Range range("lbm_step");
-    int rc = ready(c);
-    if (rc) return rc;
-    CK(c, cudaSetDevice(c->device));
+// n steps as lbm_step issues them: graph replays of kGraphSteps steps when
+// graphs are on (one-step schedules), the rest as plain launches.
+int step_n(lbm_ctx* c, int n) {
     if (c->use_graphs && c->sched != 3 && n >= kGraphSteps) {
         while (n >= kGraphSteps) {
-            rc = ensure_graph(c, c->parity);
+            int rc = ensure_graph(c, c->parity);
             if (rc) return rc;
             Range replay("lbm_step: graph replay");
             CK(c, cudaGraphLaunch(c->gexec[c->parity], c->stream));
@@ -977,6 +972,15 @@ int lbm_step(lbm_ctx* c, int n) {
         }
     }
     return launch_steps(c, n);
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+    if (!c || n < 0) return LBM_EINVAL;
+    Range range("lbm_step");
+    int rc = ready(c);
+    if (rc) return rc;
+    CK(c, cudaSetDevice(c->device));
+    return step_n(c, n);
 }
 
 int lbm_sync(lbm_ctx* c) {
@@ -1233,8 +1237,10 @@ int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double*
     }
     const int parity0 = c->parity;
     const long long steps0 = c->steps, launches0 = c->launches;
-    const bool graphs0 = c->use_graphs;
-    c->use_graphs = false;
+    // every candidate is timed the way lbm_step will run it: with graphs on,
+    // over whole graph replays (the step count rounded up to kGraphSteps),
+    // after a warm-up that captures the graph
+    if (c->use_graphs) steps = (steps + kGraphSteps - 1) / kGraphSteps * kGraphSteps;
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
@@ -1243,13 +1249,13 @@ int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double*
     for (int k = 0; k < lbm::step_config_count(c->prec); ++k)
         for (int s = 0; s < lbm::kMaxSched; ++s) {
             // one lattice: the one-step launch (0) or the multi-step one (3)
-            if ((c->n == 1 && s != 0 && s != 3) || (s == 3 && !lbm::run_supported(c->prec, k))) continue;
+            if (c->n == 1 && s != 0 && s != 3) continue;
             rc = apply_schedule(c, k, s);
             if (rc) break;
-            rc = launch_steps(c, 2);
+            rc = step_n(c, c->use_graphs && s != 3 ? kGraphSteps : 2);
             if (rc) break;
             CK(c, cudaEventRecord(e0, c->stream));
-            rc = launch_steps(c, steps);
+            rc = step_n(c, steps);
             if (rc) break;
             CK(c, cudaEventRecord(e1, c->stream));
             CK(c, cudaEventSynchronize(e1));
@@ -1259,7 +1265,6 @@ int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double*
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->use_graphs = graphs0;
     if (rc) return rc;
     c->parity = parity0;
     c->steps = steps0;

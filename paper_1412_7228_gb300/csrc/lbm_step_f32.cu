@@ -8,7 +8,7 @@ namespace {
 const Entry kF32[] = {
     LBM_CFG(float, 128, 16, 512, 1), LBM_CFG(float, 64, 16, 256, 1), LBM_CFG(float, 128, 8, 256, 1),
     LBM_CFG(float, 64, 32, 512, 1),  LBM_CFG(float, 32, 32, 256, 1), LBM_CFG(float, 64, 16, 256, 2),
-    LBM_CFG(float, 64, 8, 256, 2),   LBM_CFG(float, 32, 16, 256, 2),
+    LBM_CFG(float, 64, 8, 256, 2),   LBM_CFG(float, 32, 16, 256, 2),  LBM_CFG(float, 64, 16, 512, 2),
 };
 }  // namespace
 

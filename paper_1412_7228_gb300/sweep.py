@@ -183,6 +183,8 @@ def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP
     batch = L.Batch([d.L for d in droplets], [d.L for d in droplets], precision)
     for i, d in enumerate(droplets):
         _setup(batch, i, d, s)
+    if graphs:
+        batch.use_graphs(True)   # first: the autotuner times the schedules as they will run
     tune = None
     if schedule is not None:
         batch.set_schedule(*schedule)
@@ -190,8 +192,6 @@ def run_batch(droplets: Sequence[Droplet], steps: int, precision: int = L.LBM_FP
         # enough steps that the multi-step schedule's launch is measured over
         # many steps, as a long sweep runs it
         tune = batch.autotune(40)
-    if graphs:
-        batch.use_graphs(True)
     acc = None
     span, every = window if window else (0, 1)
     if span >= steps or span % every:
