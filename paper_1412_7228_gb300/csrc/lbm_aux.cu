@@ -21,28 +21,53 @@ template <typename T> __device__ __forceinline__ long long at(const Inst* I, int
     return a * I->plane + static_cast<long long>(y + GY) * I->pitch + (x + Prec<T>::GX);
 }
 
+// Node loops over a lattice: rows y by blockIdx.y, columns x by the
+// threads of blockIdx.x (grid from grid_2d), so that no thread divides by
+// the lattice width.
+#define LBM_FOR_NODES(nx, ny)                                      \
+    for (int y = blockIdx.y; y < (ny); y += gridDim.y)             \
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < (nx); x += gridDim.x * blockDim.x)
+
 // ---- initial state: f_a(z) = f_eq,a(rho(z), u(z)); pull storage keeps it at z - e_a
-template <typename T>
+// REST: no velocity field given (u = 0), where the equilibrium's velocity
+// terms are exact zeros and the deviation is t_a (rho - rho_ref): FP64
+// keeps the FP64 products; FP32 rounds rho - rho_ref (formed in FP64, so
+// that no digit of a small difference is lost) to FP32 once and multiplies
+// by the weights in FP32 (within 1.5 ulp of the correctly rounded value, and
+// two FP64 operations per node instead of seven: GB300's FP64 pipe would
+// otherwise bound the initialisation).
+template <typename T, bool REST>
 __global__ void k_init(const Inst* __restrict__ I, const double* __restrict__ rho, const double* __restrict__ ux,
                        const double* __restrict__ uy, int parity) {
     const int nx = I->nx, ny = I->ny;
-    const long long N = static_cast<long long>(nx) * ny;
     T* p = popk<T>(I, parity);
     const double rr = static_cast<double>(phys<T>(I).rho_ref);
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(i % nx), y = static_cast<int>(i / nx);
-        const double r = rho[i], u = ux ? ux[i] : 0.0, v = uy ? uy[i] : 0.0;
+    LBM_FOR_NODES(nx, ny) {
+        const long long i = static_cast<long long>(y) * nx + x;
+        const double r = rho[i], u = !REST && ux ? ux[i] : 0.0, v = !REST && uy ? uy[i] : 0.0;
         const double u2 = u * u + v * v;
+        // at rest: the three weights' products
+        const double d = r - rr;
+        T rest[3];
+        if constexpr (sizeof(T) == 4) {
+            const float df = static_cast<float>(d);
+            rest[0] = __fmul_rn(4.0f / 9.0f, df);
+            rest[1] = __fmul_rn(1.0f / 9.0f, df);
+            rest[2] = __fmul_rn(1.0f / 36.0f, df);
+        } else {
+            rest[0] = tw(0) * d;
+            rest[1] = tw(1) * d;
+            rest[2] = tw(5) * d;
+        }
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
             const double eu = cx(a) * u + cy(a) * v;
             // textbook second-order equilibrium, minus t_a rho_ref
-            const double dev = tw(a) * ((r - rr) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * u2));
+            const double dev = REST ? 0.0 : tw(a) * ((r - rr) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * u2));
             int xs = x - cx(a), ys = y - cy(a);
             xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
             ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-            p[at<T>(I, a, xs, ys)] = static_cast<T>(dev);
+            p[at<T>(I, a, xs, ys)] = REST ? rest[a == 0 ? 0 : (a < 5 ? 1 : 2)] : static_cast<T>(dev);
         }
     }
 }
@@ -52,29 +77,49 @@ __global__ void k_init(const Inst* __restrict__ I, const double* __restrict__ rh
 // velocity is not finite (the caller has zeroed *bad).
 __global__ void k_check_init(const double* __restrict__ rho, const double* __restrict__ ux,
                              const double* __restrict__ uy, long long N, double rho_max, int* bad) {
+    // on the bit patterns, as integers (no FP64 work): for rho_max > 0,
+    // 0 < r < rho_max with r finite is 0 < bits(r) < bits(rho_max) (positive
+    // doubles order as their patterns; negatives and -0 have the sign bit,
+    // NaN and inf patterns lie above every finite value); finite is an
+    // exponent field below all ones
+    const long long top = __double_as_longlong(rho_max);
+    constexpr unsigned long long kExp = 0x7ff0000000000000ull;
+    auto finite = [](double v) { return (static_cast<unsigned long long>(__double_as_longlong(v)) & kExp) != kExp; };
     int b = 0;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const double r = rho[i];
-        if (!(r > 0.0) || !(r < rho_max) || !isfinite(r)) b |= 1;
-        if ((ux && !isfinite(ux[i])) || (uy && !isfinite(uy[i]))) b |= 2;
+        const long long r = __double_as_longlong(rho[i]);
+        if (!(r > 0 && r < top)) b |= 1;
+        if ((ux && !finite(ux[i])) || (uy && !finite(uy[i]))) b |= 2;
     }
     b = __reduce_or_sync(0xffffffffu, b);
     if (b && (threadIdx.x & 31) == 0) atomicOr(bad, b);
 }
 
-// Ghost cells x in [-2,0) U [nx,nx+2), y in [-2,0) U [ny,ny+2) of every plane.
+// Ghost cells x in [-2,0) U [nx,nx+2), y in [-2,0) U [ny,ny+2) of every
+// plane, and only those: per plane the rows y = -2, -1, ny, ny + 1 over
+// x in [-2, nx + 2) (4 (nx + 4) cells), then the columns x = -2, -1, nx,
+// nx + 1 over y in [0, ny) (4 ny cells).  Each copies its periodic image
+// inside the lattice.
 template <typename T> __global__ void k_ghosts(const Inst* __restrict__ I, int parity) {
     const int nx = I->nx, ny = I->ny;
-    const int W = nx + 4, H = ny + 4;
-    const long long M = static_cast<long long>(W) * H * 9;
+    const int W = nx + 4, per = 4 * W + 4 * ny;
+    const long long M = 9ll * per;
     T* p = popk<T>(I, parity);
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < M;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int a = static_cast<int>(i / (static_cast<long long>(W) * H));
-        const long long r = i % (static_cast<long long>(W) * H);
-        const int x = static_cast<int>(r % W) - 2, y = static_cast<int>(r / W) - 2;
-        if (x >= 0 && x < nx && y >= 0 && y < ny) continue;
+        const int a = static_cast<int>(i / per);
+        const int r = static_cast<int>(i - static_cast<long long>(a) * per);
+        int x, y;
+        if (r < 4 * W) {
+            const int row = r / W;
+            x = r - row * W - 2;
+            y = row < 2 ? row - 2 : ny + row - 2;
+        } else {
+            const int q = r - 4 * W, col = q / ny;
+            y = q - col * ny;
+            x = col < 2 ? col - 2 : nx + col - 2;
+        }
         const int xs = ((x % nx) + nx) % nx, ys = ((y % ny) + ny) % ny;
         p[at<T>(I, a, x, y)] = p[at<T>(I, a, xs, ys)];
     }
@@ -84,14 +129,11 @@ template <typename T> __global__ void k_ghosts(const Inst* __restrict__ I, int p
 template <typename T>
 __global__ void k_gather(const Inst* __restrict__ I, int parity, int a, double* __restrict__ out) {
     const int nx = I->nx, ny = I->ny;
-    const long long N = static_cast<long long>(nx) * ny;
     const T* p = popk<T>(I, parity);
     const double off = tw(a) * static_cast<double>(phys<T>(I).rho_ref);
     const int ex = cx(a), ey = cy(a);
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(i % nx), y = static_cast<int>(i / nx);
-        out[i] = static_cast<double>(p[at<T>(I, a, x - ex, y - ey)]) + off;
+    LBM_FOR_NODES(nx, ny) {
+        out[static_cast<long long>(y) * nx + x] = static_cast<double>(p[at<T>(I, a, x - ex, y - ey)]) + off;
     }
 }
 
@@ -109,6 +151,26 @@ __device__ __forceinline__ double node_rho(const Inst* I, const T* p, int x, int
     if (jx) *jx = mx;
     if (jy) *jy = my;
     return r + static_cast<double>(phys<T>(I).rho_ref);
+}
+
+// rho of an FP32 node from its nine deviations: their sum as an unevaluated
+// pair hi + lo (Knuth's TwoSum gives the exact error of each addition; the
+// errors are summed in FP32), then hi + lo + rho_ref in FP64.  Within about
+// 2^-45 of the FP64 sum relative to the deviations' sum, and three FP64
+// operations per node instead of eighteen: GB300's FP64 pipe would
+// otherwise bound the density read-back.
+__device__ __forceinline__ double node_rho_f32(const Inst* I, const float* p, int x, int y) {
+    float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const float v = p[at<float>(I, a, x - cx(a), y - cy(a))];
+        const float sum = __fadd_rn(hi, v);
+        const float bv = __fsub_rn(sum, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bv)), __fsub_rn(v, bv));
+        hi = sum;
+        lo = __fadd_rn(lo, err);
+    }
+    return (static_cast<double>(hi) + static_cast<double>(lo)) + static_cast<double>(I->pf.rho_ref);
 }
 
 __device__ __forceinline__ double psi_of(const Phys<double>& P, double rho) {
@@ -148,26 +210,30 @@ __device__ void node_fields(const Inst* I, const T* p, int x, int y, double* rho
     *psi = ps;
 }
 
-template <typename T>
-__global__ void k_field(const Inst* __restrict__ I, int parity, int field, double* __restrict__ out) {
-    const int nx = I->nx, ny = I->ny;
-    const long long N = static_cast<long long>(nx) * ny;
+// One macroscopic field per launch (0 rho, 1 u_x, 2 u_y, 3 psi), each its
+// own kernel: the density read-back keeps the registers of a plain gather.
+// Rows [y0, y1) of the field, at their place in out (row-major nx x ny).
+template <typename T, int FIELD>
+__global__ void k_field(const Inst* __restrict__ I, int parity, int y0, int y1, double* __restrict__ out) {
+    const int nx = I->nx;
     const T* p = popk<T>(I, parity);
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(i % nx), y = static_cast<int>(i / nx);
-        double v;
-        if (field == 0) {
-            v = node_rho<T>(I, p, x, y, nullptr, nullptr);
-        } else if (field == 3) {
-            v = I->pd.interact ? psi_of(I->pd, node_rho<T>(I, p, x, y, nullptr, nullptr)) : 0.0;
-        } else {
-            double r, u, w, s;
-            node_fields<T>(I, p, x, y, &r, &u, &w, &s);
-            v = field == 1 ? u : w;
+    for (int y = y0 + static_cast<int>(blockIdx.y); y < y1; y += gridDim.y)
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+            const long long i = static_cast<long long>(y) * nx + x;
+            double v;
+            if constexpr (FIELD == 0 && sizeof(T) == 4) {
+                v = node_rho_f32(I, p, x, y);
+            } else if constexpr (FIELD == 0) {
+                v = node_rho<T>(I, p, x, y, nullptr, nullptr);
+            } else if constexpr (FIELD == 3) {
+                v = I->pd.interact ? psi_of(I->pd, node_rho<T>(I, p, x, y, nullptr, nullptr)) : 0.0;
+            } else {
+                double r, u, w, s;
+                node_fields<T>(I, p, x, y, &r, &u, &w, &s);
+                v = FIELD == 1 ? u : w;
+            }
+            out[i] = v;
         }
-        out[i] = v;
-    }
 }
 
 // ---- FP64 block reductions ----------------------------------------------
@@ -266,6 +332,18 @@ int grid_for(long long n) {
     return static_cast<int>(b);
 }
 
+// Grid of the node loops (LBM_FOR_NODES): up to 8 blocks across a row, the
+// rest down the rows, 8 * kReduceBlocks blocks at most.
+dim3 grid_2d(int nx, int ny) {
+    int gx = (nx + kThreads - 1) / kThreads;
+    if (gx > 8) gx = 8;
+    if (gx < 1) gx = 1;
+    int gy = 8 * kReduceBlocks / gx;
+    if (gy > ny) gy = ny;
+    if (gy < 1) gy = 1;
+    return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
+}
+
 // ---- the FP64 step's division, reciprocal and square root against IEEE --
 // Distance in units in the last place; values of opposite sign or NaN count
 // as infinitely far.
@@ -361,11 +439,12 @@ cudaError_t aux_fp64_fma_rate(int iters, cudaStream_t st, double* flops_per_s, d
 
 cudaError_t aux_init(const Inst& h, const Inst* d, const double* rho, const double* ux, const double* uy,
                      int parity, cudaStream_t st) {
-    const long long N = static_cast<long long>(h.nx) * h.ny;
-    if (h.prec == LBM_FP32)
-        k_init<float><<<grid_for(N), kThreads, 0, st>>>(d, rho, ux, uy, parity);
-    else
-        k_init<double><<<grid_for(N), kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    const dim3 g = grid_2d(h.nx, h.ny);
+    const bool rest = !ux && !uy;
+    if (h.prec == LBM_FP32 && rest) k_init<float, true><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    else if (h.prec == LBM_FP32) k_init<float, false><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    else if (rest) k_init<double, true><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    else k_init<double, false><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return aux_fill_ghosts(h, d, parity, st);
@@ -378,7 +457,7 @@ cudaError_t aux_check_init(const double* rho, const double* ux, const double* uy
 }
 
 cudaError_t aux_fill_ghosts(const Inst& h, const Inst* d, int parity, cudaStream_t st) {
-    const long long M = static_cast<long long>(h.nx + 4) * (h.ny + 4) * 9;
+    const long long M = 9ll * (4 * (h.nx + 4) + 4 * h.ny);
     if (h.prec == LBM_FP32)
         k_ghosts<float><<<grid_for(M), kThreads, 0, st>>>(d, parity);
     else
@@ -387,20 +466,24 @@ cudaError_t aux_fill_ghosts(const Inst& h, const Inst* d, int parity, cudaStream
 }
 
 cudaError_t aux_gather_plane(const Inst& h, const Inst* d, int parity, int a, double* out, cudaStream_t st) {
-    const long long N = static_cast<long long>(h.nx) * h.ny;
     if (h.prec == LBM_FP32)
-        k_gather<float><<<grid_for(N), kThreads, 0, st>>>(d, parity, a, out);
+        k_gather<float><<<grid_2d(h.nx, h.ny), kThreads, 0, st>>>(d, parity, a, out);
     else
-        k_gather<double><<<grid_for(N), kThreads, 0, st>>>(d, parity, a, out);
+        k_gather<double><<<grid_2d(h.nx, h.ny), kThreads, 0, st>>>(d, parity, a, out);
     return cudaGetLastError();
 }
 
-cudaError_t aux_field(const Inst& h, const Inst* d, int parity, int field, double* out, cudaStream_t st) {
-    const long long N = static_cast<long long>(h.nx) * h.ny;
-    if (h.prec == LBM_FP32)
-        k_field<float><<<grid_for(N), kThreads, 0, st>>>(d, parity, field, out);
-    else
-        k_field<double><<<grid_for(N), kThreads, 0, st>>>(d, parity, field, out);
+cudaError_t aux_field(const Inst& h, const Inst* d, int parity, int field, int y0, int y1, double* out,
+                      cudaStream_t st) {
+    const dim3 g = grid_2d(h.nx, y1 - y0);
+    auto go = [&](auto k) { k<<<g, kThreads, 0, st>>>(d, parity, y0, y1, out); };
+    const bool f32 = h.prec == LBM_FP32;
+    switch (field) {
+    case 0: f32 ? go(k_field<float, 0>) : go(k_field<double, 0>); break;
+    case 1: f32 ? go(k_field<float, 1>) : go(k_field<double, 1>); break;
+    case 2: f32 ? go(k_field<float, 2>) : go(k_field<double, 2>); break;
+    default: f32 ? go(k_field<float, 3>) : go(k_field<double, 3>); break;
+    }
     return cudaGetLastError();
 }
 

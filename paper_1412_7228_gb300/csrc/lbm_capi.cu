@@ -34,6 +34,8 @@ struct Range {
     Range& operator=(const Range&) = delete;
 };
 constexpr int kGraphSteps = 32;                            // steps per captured graph (even)
+constexpr int kReadBands = 8;                              // row bands of a field read-back
+constexpr size_t kReadBandMin = size_t(1) << 20;           // nodes from which the read-back is banded
 
 // The TMA tensor maps of one instance's two time levels (host copies; the
 // kernels receive them in their argument blocks).
@@ -241,6 +243,10 @@ struct lbm_ctx {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     lbm::StepArgs<float> one_f{};    // kernel argument block of a one-lattice context
     lbm::StepArgs<double> one_d{};
+    // field read-back of a large lattice: row bands computed on `stream`
+    // while the bands before them are copied to the host on copy_stream
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t band_done[kReadBands] = {};
     std::string err;
 };
 
@@ -856,6 +862,12 @@ void lbm_destroy(lbm_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream || c->buf) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    for (auto& e : c->band_done)
+        if (e) cudaEventDestroy(e);
     if (c->owns && c->buf) cudaFree(c->buf);
     delete c;
 }
@@ -1012,13 +1024,34 @@ int lbm_batch_read_fields(lbm_ctx* c, int i, double* rho, double* ux, double* uy
     if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
     Range range("lbm_batch_read_fields");
     CK(c, cudaSetDevice(c->device));
-    const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
+    const int nx = c->nx[i], ny = c->ny[i];
+    const size_t N = static_cast<size_t>(nx) * ny;
+    // a large lattice in row bands: band b's copy to the host overlaps band b + 1's kernel
+    const int bands = N >= kReadBandMin && ny >= kReadBands ? kReadBands : 1;
+    if (bands > 1 && !c->copy_stream) {
+        CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (auto& e : c->band_done) CK(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     double* outs[4] = {rho, ux, uy, psi};
     for (int f = 0; f < 4; ++f) {
         if (!outs[f]) continue;
-        CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, c->d_scratch, c->stream));
-        CK(c, cudaMemcpyAsync(outs[f], c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
+        if (bands == 1) {
+            CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, 0, ny, c->d_scratch, c->stream));
+            CK(c, cudaMemcpyAsync(outs[f], c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(c, cudaStreamSynchronize(c->stream));
+            continue;
+        }
+        for (int b = 0; b < bands; ++b) {
+            const int y0 = static_cast<int>(static_cast<long long>(ny) * b / bands);
+            const int y1 = static_cast<int>(static_cast<long long>(ny) * (b + 1) / bands);
+            const size_t off = static_cast<size_t>(y0) * nx, cnt = static_cast<size_t>(y1 - y0) * nx;
+            CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, y0, y1, c->d_scratch, c->stream));
+            CK(c, cudaEventRecord(c->band_done[b], c->stream));
+            CK(c, cudaStreamWaitEvent(c->copy_stream, c->band_done[b], 0));
+            CK(c, cudaMemcpyAsync(outs[f] + off, c->d_scratch + off, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->copy_stream));
+        }
+        CK(c, cudaStreamSynchronize(c->copy_stream));   // before the next field reuses the scratch
     }
     int code = LBM_OK;
     rc = status_of(c, i, &code);

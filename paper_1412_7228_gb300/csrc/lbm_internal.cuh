@@ -348,8 +348,9 @@ cudaError_t aux_check_init(const double* rho, const double* ux, const double* uy
                            int* bad, cudaStream_t st);
 cudaError_t aux_gather_plane(const Inst& host, const Inst* d_inst, int parity, int a, double* out,
                              cudaStream_t st);
-// field: 0 rho, 1 ux, 2 uy, 3 psi
-cudaError_t aux_field(const Inst& host, const Inst* d_inst, int parity, int field, double* out,
+// field: 0 rho, 1 ux, 2 uy, 3 psi; rows [y0, y1), written at their place in
+// out (row-major, nx per row)
+cudaError_t aux_field(const Inst& host, const Inst* d_inst, int parity, int field, int y0, int y1, double* out,
                       cudaStream_t st);
 // out: 4 device words (see lbm_fp64_math_check); default stream.
 cudaError_t aux_math_check(long long n, double lo, double hi, unsigned long long* out);

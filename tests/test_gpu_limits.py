@@ -146,6 +146,33 @@ def test_lattice_with_more_than_2_31_population_elements(P):
     assert worst <= 1e-6, worst
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_banded_read_back_of_a_large_lattice_matches_the_oracle_macro(P, prec):
+    """A lattice of over 2^20 nodes reads its fields back in row bands (a
+    band's copy to the host overlapping the next band's kernel; 1030 rows do
+    not split evenly into eight): every node's rho, u and psi agree with the
+    oracle's macroscopic fields of the same populations, and the initial
+    state at rest is t_a rho_ref + t_a (rho - rho_ref) per population."""
+    eos, op, rg, rl = _cs(P)
+    nx, ny = 1040, 1030
+    rho0 = I.droplet_density(nx, ny, 200, rl, rg)
+    lat = P.Lattice(nx, ny, prec)
+    lat.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=rg)
+    lat.init_density(rho0)
+    f0 = lat.read_populations()
+    rest = O.init_equilibrium(rho0)
+    assert float(np.abs(f0 - rest).max() / np.abs(rest).max()) <= (1e-15 if prec == 2 else 1e-7)
+    lat.step(6)
+    f = lat.read_populations()
+    got = lat.read_fields()
+    lat.close()
+    rho, ux, uy, psi = O.macro(op, f)[:4]
+    assert float(np.abs(got["rho"] / rho - 1).max()) <= 1e-13
+    assert float(np.abs(got["psi"] / psi - 1).max()) <= 1e-13
+    assert float(np.abs(ux).max()) > 1e-6   # the drop has started to move
+    assert float(np.abs(got["ux"] - ux).max()) <= 1e-14 and float(np.abs(got["uy"] - uy).max()) <= 1e-14
+
+
 def test_read_fields_into_caller_arrays(P):
     """read_fields fills caller-supplied (here pinned) arrays with the same
     values it returns in fresh ones, and rejects a wrong shape or dtype."""
