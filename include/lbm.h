@@ -239,10 +239,10 @@ int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads, int* s
  * (step, tile) items in step order from a counter in device memory and start
  * step s of a tile once every tile within two nodes of it (periodic) has
  * finished step s - 1 (each dependency wait bounded; one that gives up reports
- * LBM_ETIMEOUT); the launch is cooperative (every CTA resident), and CUDA
- * graphs are not used with it.  With a two-stage tile configuration each CTA
- * loads its next item's box while it collides the current one.  Every
- * schedule gives the same bits. */
+ * LBM_ETIMEOUT); the launch is cooperative (every CTA resident), needs a
+ * tile configuration of one tile box per CTA (stages 1; LBM_EINVAL
+ * otherwise), and CUDA graphs are not used with it.  Every schedule gives the
+ * same bits. */
 int lbm_set_schedule(lbm_ctx* ctx, int tile_config, int schedule);
 /* Time every (tile configuration, schedule) pair over `steps` steps of the
  * current state (which is restored afterwards) and keep the fastest (one

@@ -84,7 +84,9 @@ __global__ void k_check_init(const double* __restrict__ rho, const double* __res
     // exponent field below all ones
     const long long top = __double_as_longlong(rho_max);
     constexpr unsigned long long kExp = 0x7ff0000000000000ull;
-    auto finite = [](double v) { return (static_cast<unsigned long long>(__double_as_longlong(v)) & kExp) != kExp; };
+    auto finite = [](double v) {
+        return (static_cast<unsigned long long>(__double_as_longlong(v)) & kExp) != kExp;
+    };
     int b = 0;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {

@@ -537,6 +537,8 @@ cudaError_t launch_step(lbm_ctx* c, int parity) {
 }
 
 int apply_schedule(lbm_ctx* c, int cfg, int sched) {
+    if (sched == 3 && !lbm::run_supported(c->prec, cfg))
+        return fail(c, LBM_EINVAL, "the multi-step schedule needs a tile configuration of one box per CTA%s");
     c->cfg = cfg;
     c->sched = sched;
     drop_graphs(c);
@@ -1028,9 +1030,20 @@ int lbm_batch_read_fields(lbm_ctx* c, int i, double* rho, double* ux, double* uy
     const size_t N = static_cast<size_t>(nx) * ny;
     // a large lattice in row bands: band b's copy to the host overlaps band b + 1's kernel
     const int bands = N >= kReadBandMin && ny >= kReadBands ? kReadBands : 1;
-    if (bands > 1 && !c->copy_stream) {
-        CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-        for (auto& e : c->band_done) CK(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (bands > 1 && !c->copy_stream) {   // created once, whole or not at all
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev[kReadBands] = {};
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int b = 0; b < kReadBands && e == cudaSuccess; ++b)
+            e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (auto x : ev)
+                if (x) cudaEventDestroy(x);
+            if (cs) cudaStreamDestroy(cs);
+            return cuda_fail(c, e, "read-back copy stream");
+        }
+        c->copy_stream = cs;
+        std::copy(ev, ev + kReadBands, c->band_done);
     }
     double* outs[4] = {rho, ux, uy, psi};
     for (int f = 0; f < 4; ++f) {
@@ -1282,7 +1295,7 @@ int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double*
     for (int k = 0; k < lbm::step_config_count(c->prec); ++k)
         for (int s = 0; s < lbm::kMaxSched; ++s) {
             // one lattice: the one-step launch (0) or the multi-step one (3)
-            if (c->n == 1 && s != 0 && s != 3) continue;
+            if ((c->n == 1 && s != 0 && s != 3) || (s == 3 && !lbm::run_supported(c->prec, k))) continue;
             rc = apply_schedule(c, k, s);
             if (rc) break;
             rc = step_n(c, c->use_graphs && s != 3 ? kGraphSteps : 2);

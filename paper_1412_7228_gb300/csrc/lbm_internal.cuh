@@ -333,9 +333,10 @@ cudaError_t step_prepare(int prec, int k);   // sets the dynamic smem attribute
 // instances, T the context's precision.  ntiles: tiles this launch steps.
 cudaError_t step_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int parity,
                         unsigned long long timeout_ns, cudaStream_t st);
-// Multi-step persistent launch of tile configuration k: args a RunArgs<T>,
-// one = a single instance.  The caller has zeroed the step counters, the
-// work counter and the abort flag.
+// Multi-step persistent launch of tile configuration k (one box per CTA
+// only; false otherwise): args a RunArgs<T>, one = a single instance.  The
+// caller has zeroed the step counters, the work counter and the abort flag.
+bool run_supported(int prec, int k);
 cudaError_t run_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int nsteps,
                        unsigned long long timeout_ns, cudaStream_t st);
 

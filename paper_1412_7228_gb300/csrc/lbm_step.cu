@@ -43,6 +43,12 @@ cudaError_t step_launch(int prec, int k, const Inst* d_insts, const void* args, 
     return e[k].launch(d_insts, args, one, ntiles, parity, timeout_ns, st);
 }
 
+bool run_supported(int prec, int k) {
+    int n;
+    const Entry* e = table(prec, &n);
+    return k >= 0 && k < n && e[k].nbuf == 1;
+}
+
 cudaError_t run_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int nsteps,
                        unsigned long long timeout_ns, cudaStream_t st) {
     int n;

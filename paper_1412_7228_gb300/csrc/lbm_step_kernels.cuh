@@ -44,7 +44,6 @@ template <typename T, int BX_, int BY_, int NT_, int NBUF_> struct Geom {
     static constexpr size_t psi_off = NBUF * buf_stride;
     static constexpr size_t psi_stride = (size_t(WP) * HP * sizeof(T) + 127) / 128 * 128;   // psi tiles
     static constexpr size_t smem = psi_off + NBUF * psi_stride;
-    static constexpr size_t run_smem = psi_off + psi_stride;                // multi-step kernels: one psi tile
     static_assert(NT % BX == 0 && BY % TY == 0, "thread layout must tile the block");
     static_assert(WB <= 256 && HB <= 256, "TMA box dimensions are limited to 256");
     static_assert((WB * sizeof(T)) % 16 == 0, "TMA box rows must be a multiple of 16 bytes");
@@ -842,173 +841,6 @@ __device__ __forceinline__ void run_body(const Inst* __restrict__ insts, unsigne
     }
 }
 
-// Multi-step persistent body with two box buffers per CTA: the same work
-// items, dependencies, per-node code and bits as run_body, but the next
-// item's dependencies and TMA load overlap the current item.  Before the psi
-// ring of item k, warp 0 reads the step counters item k + 1 depends on and
-// draws item k + 2 from the counter (its value is first needed an item
-// later, so the atomic's latency is hidden); after the ring barrier, if the
-// counters were all met, it issues item k + 1's box into the other buffer
-// (free since item k - 1 ended), so the load lands while item k collides.
-// Otherwise (typically an item that depends on the CTA's own item k) warp 0
-// waits for them, bounded, after item k is published, as run_body does.  A
-// CTA holds at most three items, all handed out in step order, and the one it
-// waits for never depends on an unpublished item of its own: the schedule
-// stays deadlock-free under the cooperative launch.
-template <typename T, int BX, int BY, int NT, bool ONE>
-__device__ __forceinline__ void run_body2(const Inst* __restrict__ insts, unsigned long long timeout_ns,
-                                          const RunArgs<T>& a) {
-    using Gm = Geom<T, BX, BY, NT, 2>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_work[2][6];   // per buffer: item loading (1) or none (0), step, tile, slot, x0, y0
-    __shared__ int s_defer[2];     // per buffer: its item waits for its dependencies after the current one
-    const int tid = threadIdx.x;
-    const int tx = tid % BX, ty = tid / BX;
-    const int lane = tid & 31;
-    T* sp = reinterpret_cast<T*>(smem + Gm::psi_off);   // one psi tile: filled after the previous collision
-    const long long total = static_cast<long long>(a.nsteps) * a.ntiles;
-    // lane 0 of warp 0: the next item this CTA takes, and the one after it,
-    // both already drawn from the counter
-    long long next = 0, ahead = 0;
-
-    // lane 0: the box of item `it` into buffer bb
-    auto issue = [&](int bb, const RunItem& it) {
-        fence_proxy_async_global();   // the neighbours' stores, then this CTA's TMA read of them
-        mbar_arrive_expect_tx(&bar[bb], static_cast<uint32_t>(Gm::box_bytes));
-        tma_load_3d(smem + bb * Gm::buf_stride, &a.tmap[(a.parity0 + it.s) & 1][it.slot],
-                    it.col * BX + Gm::GX - Gm::HX, it.row * BY, 0, &bar[bb]);
-    };
-    auto record = [&](int bb, int state, const RunItem& it) {
-        s_work[bb][0] = state;
-        s_work[bb][1] = it.s;
-        s_work[bb][2] = it.t;
-        s_work[bb][3] = it.slot;
-        s_work[bb][4] = it.col * BX;
-        s_work[bb][5] = it.row * BY;
-    };
-    // warp 0: item `next` into buffer bb once its dependencies are met
-    // (bounded wait); s_work[bb] says whether it was issued
-    auto take = [&](int bb) {
-        const long long w = __shfl_sync(0xffffffffu, next, 0);
-        int ok = w < total;
-        if (lane == 0 && ok) ok = ld_acquire_gpu(a.abort_flag) == 0;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        RunItem it{0, 0, 0, 0, 0};
-        if (ok) {
-            it = run_item<ONE>(a, w);
-            if (it.s > 0) {
-                const int* flag = lane < 16 ? run_dep_flag<BX, BY>(a, it, lane) : nullptr;
-                ok = run_dep_wait(flag, lane >= 16 || ld_acquire_gpu(flag) >= it.s, it.s, a.abort_flag, timeout_ns);
-                if (!ok && lane == 0) {
-                    atomicExch(a.abort_flag, 1);
-                    atomicOr(a.lat[it.slot].status, ST_TIMEOUT);
-                }
-            }
-        }
-        if (lane == 0) {
-            if (ok) issue(bb, it);
-            record(bb, ok, it);
-        }
-    };
-
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        next = static_cast<long long>(atomicAdd(a.counter, 1ull));
-    }
-    if (tid < 32) {
-        __syncwarp();
-        take(0);
-        if (lane == 0) ahead = static_cast<long long>(atomicAdd(a.counter, 1ull));
-    }
-    __syncthreads();
-
-#pragma unroll 1
-    for (int k = 0;; ++k) {
-        const int b = k & 1;
-        if (!s_work[b][0]) break;   // no item, and none in flight in the other buffer
-        const int s = s_work[b][1], t = s_work[b][2], slot = ONE ? 0 : s_work[b][3];
-        const int x0 = s_work[b][4], y0 = s_work[b][5];
-
-        // warp 0: the item after this one (drawn an item ago), the counters it
-        // depends on and the abort flag, read now and looked at after the ring
-        // (the loads are in flight meanwhile); and the item after that
-        int pre_ok = 0, pre_v = 0x7fffffff, pre_abort = 0;
-        RunItem pre{0, 0, 0, 0, 0};
-        if (tid < 32) {
-            if (lane == 0) {
-                next = ahead;
-                ahead = static_cast<long long>(atomicAdd(a.counter, 1ull));
-            }
-            const long long w = __shfl_sync(0xffffffffu, next, 0);
-            pre_ok = w < total;
-            if (pre_ok) {
-                pre = run_item<ONE>(a, w);
-                if (lane == 0) pre_abort = ld_acquire_gpu(a.abort_flag);
-                if (pre.s > 0 && lane < 16) pre_v = ld_acquire_gpu(run_dep_flag<BX, BY>(a, pre, lane));
-            }
-        }
-
-        const T* sf = reinterpret_cast<const T*>(smem + b * Gm::buf_stride);
-        const int parity = (a.parity0 + s) & 1;
-        const Inst* I = nullptr;
-        if constexpr (sizeof(T) == 8) I = insts + a.inst[slot];
-        const Phys<T>& P = phys_of(a, I, slot);
-        const int nx = a.lat[slot].nx, ny = a.lat[slot].ny;
-        int* const status = a.lat[slot].status;
-        T* const dst = static_cast<T*>(a.lat[slot].pop[parity ^ 1]);
-        const long long plane = a.lat[slot].plane;
-        const int pitch = a.lat[slot].pitch;
-        const int interact = P.interact;
-        const EosRegs<T> E(P);
-        const T rho_ref = P.rho_ref;
-        const bool border = x0 < 2 || x0 + BX > nx - 2 || y0 < 2 || y0 + BY > ny - 2;
-        const bool fast = interact && !P.var_visc && x0 + BX <= nx && y0 + BY <= ny;
-
-        const uint32_t ph = (k >> 1) & 1;   // uses of this buffer's barrier so far
-        bool ok = mbar_wait_bounded(&bar[b], ph, timeout_ns);
-        if (k == 0 && (P.flags & LBM_FLAG_TEST_FORCE_TIMEOUT)) {
-            // the phase after the completed load: nothing completes it
-            ok = ok && mbar_wait_bounded(&bar[0], 1, 2000000ull);
-        }
-        if (interact && ok) ring_dispatch<Gm>(fast, P.eos, sf, sp, E, rho_ref, tid, tx, ty);
-        if (!__syncthreads_and(ok)) {
-            // nothing was issued into the other buffer yet
-            if (tid == 0) {
-                atomicOr(status, ST_TIMEOUT);
-                atomicExch(a.abort_flag, 1);
-                mbar_wait_bounded(&bar[b], ph, timeout_ns);   // let a late copy land before exit
-            }
-            return;
-        }
-        // warp 0: issue the next item now if its dependencies were met (the
-        // barrier above orders the lanes' acquires before lane 0's issue),
-        // else defer it to after this item's publication
-        if (tid < 32) {
-            pre_ok = pre_ok && __shfl_sync(0xffffffffu, pre_abort, 0) == 0;
-            const bool early = pre_ok && __all_sync(0xffffffffu, pre_v >= pre.s);
-            if (lane == 0) {
-                if (early) issue(b ^ 1, pre);
-                record(b ^ 1, early, pre);
-                s_defer[b ^ 1] = pre_ok && !early;
-            }
-        }
-
-        const Regs<T> R(P);
-        const bool bad = collide_dispatch<Gm>(fast, border, sf, sp, P, R, dst, plane, pitch, x0, y0, nx, ny, interact,
-                                              tx, ty);
-        if (bad) atomicOr(status, ST_UNSTABLE);
-        __syncthreads();   // every store of the tile, and every read of both its box and the psi tile, is done
-        if (tid == 32) st_release_gpu(a.done + t, s + 1);   // cumulative over the barrier, as in run_body
-        if (s_defer[b ^ 1]) {   // the same for every thread: written before the barrier above
-            if (tid < 32) take(b ^ 1);
-            __syncthreads();
-        }
-    }
-}
-
 // The kernels.  FP32 launches ask for 1024 resident threads per SM (two
 // CTAs of 512), which caps their registers at 64 (except the batched
 // persistent variant, which would spill); FP64 leaves the register count to
@@ -1036,46 +868,39 @@ __global__ void __launch_bounds__(NT, (ONE || NBUF == 1) ? 1024 / NT : 1) k_step
                                                             const __grid_constant__ ArgsOf<float, ONE> args) {
     step_body<float, BX, BY, NT, NBUF, ONE>(insts, ntiles, parity, timeout_ns, args);
 }
-// one box buffer (run_body) or two (run_body2)
-template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
-__device__ __forceinline__ void run_any(const Inst* __restrict__ insts, unsigned long long timeout_ns,
-                                        const RunArgs<T>& args) {
-    if constexpr (NBUF == 1) run_body<T, BX, BY, NT, ONE>(insts, timeout_ns, args);
-    else run_body2<T, BX, BY, NT, ONE>(insts, timeout_ns, args);
-}
-template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
+template <typename T, int BX, int BY, int NT, bool ONE>
 __global__ void __launch_bounds__(NT, 2) k_run(const Inst* __restrict__ insts, unsigned long long timeout_ns,
                                             const __grid_constant__ RunArgs<T> args) {
-    run_any<T, BX, BY, NT, NBUF, ONE>(insts, timeout_ns, args);
+    run_body<T, BX, BY, NT, ONE>(insts, timeout_ns, args);
 }
-template <typename T, int BX, int BY, int NT, int NBUF, bool ONE>
+template <typename T, int BX, int BY, int NT, bool ONE>
 __global__ void __launch_bounds__(NT, 3) k_run_row(const Inst* __restrict__ insts, unsigned long long timeout_ns,
                                                    const __grid_constant__ RunArgs<T> args) {
-    run_any<T, BX, BY, NT, NBUF, ONE>(insts, timeout_ns, args);
+    run_body<T, BX, BY, NT, ONE>(insts, timeout_ns, args);
 }
 // CTAs of the multi-step FP32 kernel that fit on an SM: 1024 threads, and
 // the SM's 228 KB of shared memory (1 KB of it reserved per CTA)
-template <int BX, int BY, int NT, int NBUF> constexpr int run_ctas_f32() {
-    constexpr int by_smem = static_cast<int>(233472 / (Geom<float, BX, BY, NT, NBUF>::run_smem + 2048));
+template <int BX, int BY, int NT> constexpr int run_ctas_f32() {
+    constexpr int by_smem = static_cast<int>(233472 / (Geom<float, BX, BY, NT, 1>::smem + 2048));
     return by_smem < 1024 / NT ? (by_smem > 0 ? by_smem : 1) : 1024 / NT;
 }
-template <int BX, int BY, int NT, int NBUF, bool ONE>
-__global__ void __launch_bounds__(NT, (run_ctas_f32<BX, BY, NT, NBUF>())) k_run_f32(const Inst* __restrict__ insts,
-                                                           unsigned long long timeout_ns,
-                                                           const __grid_constant__ RunArgs<float> args) {
-    run_any<float, BX, BY, NT, NBUF, ONE>(insts, timeout_ns, args);
+template <int BX, int BY, int NT, bool ONE>
+__global__ void __launch_bounds__(NT, (run_ctas_f32<BX, BY, NT>())) k_run_f32(const Inst* __restrict__ insts,
+                                                                          unsigned long long timeout_ns,
+                                                                          const __grid_constant__ RunArgs<float> args) {
+    run_body<float, BX, BY, NT, ONE>(insts, timeout_ns, args);
 }
 // the multi-step kernel of a (precision, ONE) launch, with the launch bounds of the one-step kernel
-template <typename T, int BX, int BY, int NT, int NBUF, bool ONE,
-          int KIND = std::is_same<T, float>::value ? 2 : (BX * BY == NT && NBUF == 1 ? 1 : 0)>
+template <typename T, int BX, int BY, int NT, bool ONE,
+          int KIND = std::is_same<T, float>::value ? 2 : (BX * BY == NT ? 1 : 0)>
 struct RSel {
-    static constexpr auto fn = &k_run<T, BX, BY, NT, NBUF, ONE>;
+    static constexpr auto fn = &k_run<T, BX, BY, NT, ONE>;
 };
-template <typename T, int BX, int BY, int NT, int NBUF, bool ONE> struct RSel<T, BX, BY, NT, NBUF, ONE, 1> {
-    static constexpr auto fn = &k_run_row<T, BX, BY, NT, NBUF, ONE>;
+template <typename T, int BX, int BY, int NT, bool ONE> struct RSel<T, BX, BY, NT, ONE, 1> {
+    static constexpr auto fn = &k_run_row<T, BX, BY, NT, ONE>;
 };
-template <typename T, int BX, int BY, int NT, int NBUF, bool ONE> struct RSel<T, BX, BY, NT, NBUF, ONE, 2> {
-    static constexpr auto fn = &k_run_f32<BX, BY, NT, NBUF, ONE>;
+template <typename T, int BX, int BY, int NT, bool ONE> struct RSel<T, BX, BY, NT, ONE, 2> {
+    static constexpr auto fn = &k_run_f32<BX, BY, NT, ONE>;
 };
 
 // the kernel a (precision, ONE) launch uses
@@ -1095,18 +920,22 @@ template <typename T, int BX, int BY, int NT, int NBUF, bool ONE> struct KSel<T,
 template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
     using Gm = Geom<T, BX, BY, NT, NBUF>;
     static int grid_cap[2];   // resident CTAs on the device (persistent grid), per kernel variant
-    static int run_cap[2];    // resident CTAs of the multi-step kernels
+    static int run_cap[2];    // resident CTAs of the multi-step kernels (one box per CTA only)
     template <bool ONE> static cudaError_t prep_run() {
-        const auto fn = RSel<T, BX, BY, NT, NBUF, ONE>::fn;
-        cudaError_t e =
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(Gm::run_smem));
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, occ = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, Gm::run_smem)) != cudaSuccess) return e;
-        run_cap[ONE ? 1 : 0] = occ * sms;
-        return cudaSuccess;
+        if constexpr (NBUF != 1) {
+            return cudaSuccess;
+        } else {
+            const auto fn = RSel<T, BX, BY, NT, ONE>::fn;
+            cudaError_t e =
+                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(Gm::smem));
+            if (e != cudaSuccess) return e;
+            int dev = 0, sms = 0, occ = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, Gm::smem)) != cudaSuccess) return e;
+            run_cap[ONE ? 1 : 0] = occ * sms;
+            return cudaSuccess;
+        }
     }
     // every CTA of the grid resident (cooperative launch), no more CTAs than
     // work items, and no more than two per tile: beyond that the extra CTAs of
@@ -1114,24 +943,28 @@ template <typename T, int BX, int BY, int NT, int NBUF> struct Cfg {
     // finished, and hold SM slots that other launches could use
     static cudaError_t run(const Inst* d, const void* args, bool one, int ntiles, int nsteps, unsigned long long to,
                            cudaStream_t st) {
-        const long long items = static_cast<long long>(ntiles) * nsteps;
-        const int cap = run_cap[one ? 1 : 0];
-        if (cap < 1) return cudaErrorNotSupported;
-        long long grid = items < cap ? items : cap;
-        if (grid > 2ll * ntiles) grid = 2ll * ntiles;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(static_cast<unsigned>(grid));
-        cfg.blockDim = dim3(NT);
-        cfg.dynamicSmemBytes = Gm::run_smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeCooperative;
-        attr.val.cooperative = 1;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
-        const RunArgs<T>& a = *static_cast<const RunArgs<T>*>(args);
-        if (one) return cudaLaunchKernelEx(&cfg, RSel<T, BX, BY, NT, NBUF, true>::fn, d, to, a);
-        return cudaLaunchKernelEx(&cfg, RSel<T, BX, BY, NT, NBUF, false>::fn, d, to, a);
+        if constexpr (NBUF != 1) {
+            return cudaErrorNotSupported;
+        } else {
+            const long long items = static_cast<long long>(ntiles) * nsteps;
+            const int cap = run_cap[one ? 1 : 0];
+            if (cap < 1) return cudaErrorNotSupported;
+            long long grid = items < cap ? items : cap;
+            if (grid > 2ll * ntiles) grid = 2ll * ntiles;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(static_cast<unsigned>(grid));
+            cfg.blockDim = dim3(NT);
+            cfg.dynamicSmemBytes = Gm::smem;
+            cfg.stream = st;
+            cudaLaunchAttribute attr;
+            attr.id = cudaLaunchAttributeCooperative;
+            attr.val.cooperative = 1;
+            cfg.attrs = &attr;
+            cfg.numAttrs = 1;
+            const RunArgs<T>& a = *static_cast<const RunArgs<T>*>(args);
+            if (one) return cudaLaunchKernelEx(&cfg, RSel<T, BX, BY, NT, true>::fn, d, to, a);
+            return cudaLaunchKernelEx(&cfg, RSel<T, BX, BY, NT, false>::fn, d, to, a);
+        }
     }
     static TileCfg tc() { return TileCfg{BX, BY, NT, NBUF}; }
     static size_t smem() { return Gm::smem; }
@@ -1181,12 +1014,13 @@ struct Entry {
     cudaError_t (*prepare)();
     cudaError_t (*launch)(const Inst*, const void*, bool, int, int, unsigned long long, cudaStream_t);
     cudaError_t (*run)(const Inst*, const void*, bool, int, int, unsigned long long, cudaStream_t);
+    int nbuf;
 };
 
 #define LBM_CFG(T, BX, BY, NT, NB)                                                                    \
     Entry {                                                                                          \
         &Cfg<T, BX, BY, NT, NB>::tc, &Cfg<T, BX, BY, NT, NB>::smem, &Cfg<T, BX, BY, NT, NB>::prepare, \
-            &Cfg<T, BX, BY, NT, NB>::launch, &Cfg<T, BX, BY, NT, NB>::run                             \
+            &Cfg<T, BX, BY, NT, NB>::launch, &Cfg<T, BX, BY, NT, NB>::run, NB                         \
     }
 
 }  // namespace lbm
