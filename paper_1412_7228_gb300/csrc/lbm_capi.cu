@@ -22,7 +22,7 @@ namespace {
 
 constexpr unsigned long long kTimeoutNs = 1000000000ull;   // bounded TMA wait: 1 s
 #ifndef LBM_RUN_CHUNK_MB
-#define LBM_RUN_CHUNK_MB 64   // populations per multi-step launch, MiB (see build_run_chunks)
+#define LBM_RUN_CHUNK_MB 80   // populations per multi-step launch, MiB (see build_run_chunks)
 #endif
 
 // An NVTX range over the enclosing scope (host side: it brackets the calls
@@ -409,24 +409,45 @@ int build_chunks(lbm_ctx* c, std::vector<lbm::BatchArgs<T>> (&out)[2], const std
 }
 
 // Argument blocks of the multi-step launches: instances in index order, cut
-// into chunks of up to kRunMax instances whose populations (both time
-// levels) take at most kRunChunkBytes, unless one instance alone takes more;
+// into as few chunks as kRunMax instances per chunk and kRunChunkBytes of
+// populations (both time levels) per chunk allow (an instance larger than
+// that is a chunk of its own), with the bytes spread evenly over the chunks;
 // a chunk steps its instances through all the steps of one lbm_step call in
 // one launch (instances are independent), so a chunk that fits in L2 (129 MB
-// on GB300) keeps its populations there from step to step.
+// on GB300) keeps its populations there from step to step.  Even chunks
+// matter: a last chunk of a few instances has too few tiles per step for
+// the resident CTAs, which then wait on its step-to-step dependencies (60
+// droplets of 256^2 in chunks of 13 and a last one of 8: 69.7 G updates/s;
+// in four chunks of 15: 75.7).
 constexpr size_t kRunChunkBytes = static_cast<size_t>(LBM_RUN_CHUNK_MB) << 20;
 template <typename T>
 int build_run_chunks(lbm_ctx* c, std::vector<lbm::RunArgs<T>>& out, const std::vector<int>& tx,
                      const std::vector<int>& cnt) {
     int* done = reinterpret_cast<int*>(c->d_run + 16);
-    int tile0 = 0;
-    for (int c0 = 0, m = 0; c0 < c->n; c0 += m) {
+    auto bytes_of = [&](int i) { return 2 * 9 * static_cast<size_t>(c->h[i].plane) * c->esz; };
+    // the chunk count: as many as filling each chunk up to the limits needs
+    size_t left = 0;
+    int chunks = 0;
+    for (int c0 = 0, m = 0; c0 < c->n; c0 += m, ++chunks) {
         size_t bytes = 0;
         for (m = 0; c0 + m < c->n && m < lbm::kRunMax; ++m) {
-            const size_t b = 2 * 9 * static_cast<size_t>(c->h[c0 + m].plane) * c->esz;
+            const size_t b = bytes_of(c0 + m);
             if (m > 0 && bytes + b > kRunChunkBytes) break;
             bytes += b;
         }
+        left += bytes;
+    }
+    int tile0 = 0;
+    for (int c0 = 0, m = 0; c0 < c->n; c0 += m, --chunks) {
+        // this chunk's share of what is left, cut at the instance nearest to it
+        const size_t target = left / static_cast<size_t>(std::max(chunks, 1));
+        size_t bytes = 0;
+        for (m = 0; c0 + m < c->n && m < lbm::kRunMax; ++m) {
+            const size_t b = bytes_of(c0 + m);
+            if (m > 0 && (bytes + b > kRunChunkBytes || bytes + b / 2 > target)) break;
+            bytes += b;
+        }
+        left -= bytes;
         lbm::RunArgs<T> a;
         std::memset(&a, 0, sizeof a);
         a.n = m;
