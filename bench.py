@@ -229,7 +229,7 @@ def make_lattice(P, nx, ny, prec, rho0, stream=None):
     return lat
 
 
-GRAPH_STEPS = 32   # lbm_step replays a captured graph per 32 steps; a remainder runs as plain launches
+GRAPH_STEPS = 2    # lbm_step replays captured graphs of 32, 16, 8, 4 and 2 steps; an odd last step is a plain launch
 
 
 def graph_use(steps):
@@ -271,6 +271,7 @@ def plain_method_64(torch, P, steps=10000):
         lat.use_graphs(True)
         k, sch, _ = lat.autotune(40)
         lat.init_density(rho0)
+        lat.capture_graphs()
         t = time_steps(torch, lat, steps)
         lat.sync()
         lat.close()
@@ -311,6 +312,7 @@ def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
     b.use_graphs(True)
     tile, sched, _ = b.autotune(40)
     b.step(64)
+    b.capture_graphs()
     b.sync()
     t_b = time_steps(torch, b, steps)
     b.sync()
@@ -325,6 +327,7 @@ def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
         lat.use_graphs(True)
         lat.autotune(40)
         lat.step(64)
+        lat.capture_graphs()
         lats.append(lat)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -491,6 +494,7 @@ def run_ours(args):
     lat.use_graphs(True)
     launches0 = lat.kernel_launches
     lat.step(args.warmup)
+    lat.capture_graphs()   # every graph the timed steps replay, captured outside the timed region
     lat.sync()
 
     def barrier():
@@ -534,6 +538,7 @@ def run_ours(args):
         lat64.set_schedule(TILE_FP64, 0)
         lat64.use_graphs(True)
         lat64.step(min(args.warmup, 10))
+        lat64.capture_graphs()
         lat64.sync()
         k64 = max(32, args.steps // 32)
         with ClockSampler(local) as clk64:
@@ -574,6 +579,7 @@ def run_ours(args):
                 lo.init_density(rho_init)
                 lo.use_graphs(True)
                 lo.step(32)
+                lo.capture_graphs()
                 lo.sync()
                 tt = time_steps(torch, lo, nsteps)
                 lo.sync()
@@ -598,6 +604,7 @@ def run_ours(args):
         lat.use_graphs(True)
         lat.init_density(host_rho)
         lat.step(args.warmup)
+        lat.capture_graphs()
         lat.sync()
         barrier()
         t0 = time.perf_counter()

@@ -253,8 +253,18 @@ int lbm_set_schedule(lbm_ctx* ctx, int tile_config, int schedule);
  * milliseconds. */
 int lbm_autotune(lbm_ctx* ctx, int steps, int* tile_config, int* schedule, double* ms_per_step);
 
-/* CUDA graphs for lbm_step: on (1) or off (0, the default). */
+/* CUDA graphs for lbm_step: on (1) or off (0, the default).  With graphs on,
+ * the one-step schedules run lbm_step(n) as replays of captured graphs of 32
+ * steps, then of 16, 8, 4 and 2 steps as the rest's binary digits call for,
+ * and a last odd step as a plain launch; a graph is captured on its first
+ * use, and dropped when the parameters, schedule or graph setting change. */
 int lbm_use_graphs(lbm_ctx* ctx, int on);
+/* Capture, without running them, every graph lbm_step may replay for this
+ * context (each length from either time level), so that no later lbm_step
+ * pays for a capture (e.g. before a timed region).  Does nothing when graphs
+ * are off or the schedule is 3.  Returns LBM_OK, LBM_EINVAL (an instance
+ * without parameters or initial state) or LBM_ECUDA. */
+int lbm_capture_graphs(lbm_ctx* ctx);
 
 /* Steps done since the last init/load, and fused-step kernel launches
  * (graph replays count every kernel in them) since creation. */

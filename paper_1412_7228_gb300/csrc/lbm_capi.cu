@@ -33,7 +33,8 @@ struct Range {
     Range(const Range&) = delete;
     Range& operator=(const Range&) = delete;
 };
-constexpr int kGraphSteps = 32;                            // steps per captured graph (even)
+constexpr int kGraphLevels = 5;                            // captured graphs of 2, 4, ..., 32 steps
+constexpr int kGraphSteps = 2 << (kGraphLevels - 1);       // the longest: 32 steps
 constexpr int kReadBands = 8;                              // row bands of a field read-back
 constexpr size_t kReadBandMin = size_t(1) << 20;           // nodes from which the read-back is banded
 
@@ -240,7 +241,7 @@ struct lbm_ctx {
     long long steps = 0, launches = 0;
     int cfg = 0, sched = 0;
     bool use_graphs = false;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2][kGraphLevels] = {};   // [start parity][level]: 2 << level steps
     lbm::StepArgs<float> one_f{};    // kernel argument block of a one-lattice context
     lbm::StepArgs<double> one_d{};
     // field read-back of a large lattice: row bands computed on `stream`
@@ -273,8 +274,9 @@ int cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
     } while (0)
 
 void drop_graphs(lbm_ctx* c) {
-    for (auto& g : c->gexec)
-        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto& per : c->gexec)
+        for (auto& g : per)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
 int encode_maps(lbm_ctx* c) {
@@ -643,11 +645,13 @@ int launch_steps(lbm_ctx* c, int n) {
     return LBM_OK;
 }
 
-int ensure_graph(lbm_ctx* c, int parity) {
-    if (c->gexec[parity]) return LBM_OK;
+// The graph of 2 << level steps from time level `parity`, captured (not
+// run) on first use.
+int ensure_graph(lbm_ctx* c, int parity, int level) {
+    if (c->gexec[parity][level]) return LBM_OK;
     cudaGraph_t g;
     CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < kGraphSteps; ++k) {
+    for (int k = 0; k < (2 << level); ++k) {
         cudaError_t e = launch_step(c, parity ^ (k & 1));
         if (e != cudaSuccess) {
             cudaStreamEndCapture(c->stream, &g);
@@ -655,7 +659,7 @@ int ensure_graph(lbm_ctx* c, int parity) {
         }
     }
     CK(c, cudaStreamEndCapture(c->stream, &g));
-    cudaError_t e = cudaGraphInstantiate(&c->gexec[parity], g, 0);
+    cudaError_t e = cudaGraphInstantiate(&c->gexec[parity][level], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
     return LBM_OK;
@@ -992,18 +996,24 @@ int lbm_init_density(lbm_ctx* c, const double* rho, const double* ux, const doub
     return lbm_batch_init_density(c, 0, rho, ux, uy);
 }
 
-// n steps as lbm_step issues them: graph replays of kGraphSteps steps when
-// graphs are on (one-step schedules), the rest as plain launches.
+// n steps as lbm_step issues them.  With graphs on (one-step schedules):
+// replays of the 32-step graph, then of the 16-, 8-, 4- and 2-step graphs
+// the rest's binary digits call for (20 steps: two replays), and a last odd
+// step as a plain launch; every graph has an even number of steps, so the
+// parity a replay starts from is the current one.
 int step_n(lbm_ctx* c, int n) {
-    if (c->use_graphs && c->sched != 3 && n >= kGraphSteps) {
-        while (n >= kGraphSteps) {
-            int rc = ensure_graph(c, c->parity);
-            if (rc) return rc;
-            Range replay("lbm_step: graph replay");
-            CK(c, cudaGraphLaunch(c->gexec[c->parity], c->stream));
-            c->launches += static_cast<long long>(kGraphSteps) * step_launches(c);
-            c->steps += kGraphSteps;
-            n -= kGraphSteps;   // an even number of steps: parity is unchanged
+    if (c->use_graphs && c->sched != 3) {
+        for (int level = kGraphLevels - 1; level >= 0; --level) {
+            const int len = 2 << level;
+            while (n >= len && (level == kGraphLevels - 1 || n < 2 * len)) {
+                int rc = ensure_graph(c, c->parity, level);
+                if (rc) return rc;
+                Range replay("lbm_step: graph replay");
+                CK(c, cudaGraphLaunch(c->gexec[c->parity][level], c->stream));
+                c->launches += static_cast<long long>(len) * step_launches(c);
+                c->steps += len;
+                n -= len;
+            }
         }
     }
     return launch_steps(c, n);
@@ -1352,6 +1362,18 @@ int lbm_use_graphs(lbm_ctx* c, int on) {
     if (on && c->stream == nullptr) return fail(c, LBM_EINVAL, "CUDA graphs need a non-default stream%s");
     c->use_graphs = on != 0;
     if (!on) drop_graphs(c);
+    return LBM_OK;
+}
+
+int lbm_capture_graphs(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    if (!c->use_graphs || c->sched == 3) return LBM_OK;
+    int rc = ready(c);
+    if (rc) return rc;
+    CK(c, cudaSetDevice(c->device));
+    for (int parity = 0; parity < 2; ++parity)
+        for (int level = 0; level < kGraphLevels; ++level)
+            if ((rc = ensure_graph(c, parity, level))) return rc;
     return LBM_OK;
 }
 

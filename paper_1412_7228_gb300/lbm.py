@@ -38,7 +38,7 @@ EXPORTS = [
     "lbm_read_fields", "lbm_batch_read_fields", "lbm_read_populations", "lbm_batch_read_populations",
     "lbm_measure_pressure_jump", "lbm_batch_measure", "lbm_stats", "lbm_batch_stats",
     "lbm_save", "lbm_load", "lbm_tile_config_count", "lbm_tile_config", "lbm_set_schedule",
-    "lbm_autotune", "lbm_use_graphs", "lbm_steps_done", "lbm_kernel_launches", "lbm_bytes_per_update",
+    "lbm_autotune", "lbm_use_graphs", "lbm_capture_graphs", "lbm_steps_done", "lbm_kernel_launches", "lbm_bytes_per_update",
     "lbm_last_error", "lbm_field_pressure_jump_static",
     "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_set_normalization", "lbm_mlp_set_params", "lbm_mlp_get_params",
     "lbm_mlp_loss_grad", "lbm_mlp_adam_step", "lbm_mlp_train", "lbm_mlp_predict", "lbm_mlp_invert_kappa",
@@ -132,6 +132,7 @@ def lib():
         "lbm_set_schedule": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "lbm_autotune": ([_vp, ctypes.c_int, _ip, _ip, _dp], ctypes.c_int),
         "lbm_use_graphs": ([_vp, ctypes.c_int], ctypes.c_int),
+        "lbm_capture_graphs": ([_vp], ctypes.c_int),
         "lbm_steps_done": ([_vp], ctypes.c_longlong),
         "lbm_kernel_launches": ([_vp], ctypes.c_longlong),
         "lbm_bytes_per_update": ([ctypes.c_int], ctypes.c_int),
@@ -394,6 +395,10 @@ class Batch:
 
     def use_graphs(self, on: bool = True):
         self._c(lib().lbm_use_graphs(self.ctx, int(bool(on))))
+
+    def capture_graphs(self):
+        """Capture every graph step() may replay now, instead of on first use."""
+        self._c(lib().lbm_capture_graphs(self.ctx))
 
     @property
     def steps_done(self) -> int:

@@ -107,6 +107,40 @@ def test_every_tile_config_and_graphs_are_bit_identical(P):
         assert np.array_equal(gpu_run(P, prec, eos, op, rho0, 70, rho_ref=rg, graphs=True), base)
 
 
+def test_graph_replays_of_every_length_give_the_one_step_bits(P):
+    """With graphs on, lbm_step(n) replays graphs of 32, 16, 8, 4 and 2 steps
+    (the binary digits of n below 32) and launches an odd last step plainly:
+    every split of the steps into calls, with the graphs captured ahead
+    (capture_graphs) or on first use, gives the bits of plain launches and
+    counts one kernel launch per step."""
+    eos, op, rg, rl = cs_case(P)
+    rho0 = I.droplet_density(90, 75, 20, rl, rg)
+    counts = (1, 2, 3, 5, 20, 37, 64, 6)
+    base = gpu_run(P, P.LBM_FP32, eos, op, rho0, sum(counts), rho_ref=rg)
+    for ahead in (False, True):
+        lat = P.Lattice(90, 75, P.LBM_FP32)
+        lat.set_params(eos, op.A, op.kappa, G=op.G, s=op.s, rho_ref=rg)
+        lat.init_density(rho0)
+        lat.use_graphs(True)
+        if ahead:
+            lat.capture_graphs()
+        n0 = lat.kernel_launches
+        for n in counts:
+            lat.step(n)
+        assert lat.kernel_launches - n0 == sum(counts) and lat.steps_done == sum(counts)
+        lat.sync()
+        assert np.array_equal(lat.read_populations(), base), ahead
+        lat.close()
+    lat = P.Lattice(90, 75, P.LBM_FP32)   # graphs off or the multi-step schedule: nothing to capture
+    lat.set_params(eos, op.A, op.kappa, G=op.G, s=op.s, rho_ref=rg)
+    lat.init_density(rho0)
+    lat.capture_graphs()
+    lat.use_graphs(True)
+    lat.set_schedule(0, 3)
+    lat.capture_graphs()
+    lat.close()
+
+
 def test_multi_step_launch_in_pieces_and_tiny_lattices(P):
     """The multi-step schedule gives the one-step bits however the steps are
     split into calls (odd counts flip the time level inside a launch), on a
