@@ -410,7 +410,7 @@ int build_chunks(lbm_ctx* c, std::vector<lbm::BatchArgs<T>> (&out)[2], const std
     return LBM_OK;
 }
 
-// Argument blocks of the multi-step launches: instances in index order, cut
+// Argument blocks of the multi-step launches: instances largest first, cut
 // into as few chunks as kRunMax instances per chunk and kRunChunkBytes of
 // populations (both time levels) per chunk allow (an instance larger than
 // that is a chunk of its own), with the bytes spread evenly over the chunks;
@@ -426,7 +426,12 @@ template <typename T>
 int build_run_chunks(lbm_ctx* c, std::vector<lbm::RunArgs<T>>& out, const std::vector<int>& tx,
                      const std::vector<int>& cnt) {
     int* done = reinterpret_cast<int*>(c->d_run + 16);
-    auto bytes_of = [&](int i) { return 2 * 9 * static_cast<size_t>(c->h[i].plane) * c->esz; };
+    // instances largest first (index order among equal sizes), so that a
+    // chunk holds lattices of one size: its tiles per step stay even
+    std::vector<int> order(c->n);
+    for (int i = 0; i < c->n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return c->h[x].plane > c->h[y].plane; });
+    auto bytes_of = [&](int j) { return 2 * 9 * static_cast<size_t>(c->h[order[j]].plane) * c->esz; };
     // the chunk count: as many as filling each chunk up to the limits needs
     size_t left = 0;
     int chunks = 0;
@@ -455,7 +460,7 @@ int build_run_chunks(lbm_ctx* c, std::vector<lbm::RunArgs<T>>& out, const std::v
         a.n = m;
         int first = 0;
         for (int k = 0; k < m; ++k) {
-            const int i = c0 + k;
+            const int i = order[c0 + k];
             const Inst& I = c->h[i];
             a.inst[k] = i;
             a.tiles_x[k] = tx[i];
