@@ -47,7 +47,7 @@ def simulate(params: np.ndarray, L_: int, steps: int, chunk: int = 1024, precisi
     seconds, lups = 0.0, 0.0
     for c0 in range(0, len(params), chunk):
         drops = [Droplet(L_, 0.2 * L_, float(t), float(a), float(k)) for t, a, k in params[c0:c0 + chunk]]
-        info = run_batch(drops, steps, precision, autotune=False)
+        info = run_batch(drops, steps, precision)   # tile and schedule autotuned: a few seconds per chunk
         seconds += info["seconds"]
         lups += len(drops) * L_ * L_ * steps
         for i, d in enumerate(drops):
