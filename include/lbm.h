@@ -241,8 +241,15 @@ int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads, int* s
  * finished step s - 1 (each dependency wait bounded; one that gives up reports
  * LBM_ETIMEOUT); the launch is cooperative (every CTA resident), needs a
  * tile configuration of one tile box per CTA (stages 1; LBM_EINVAL
- * otherwise), and CUDA graphs are not used with it.  Every schedule gives the
- * same bits. */
+ * otherwise), and CUDA graphs are not used with it.  Schedule 4 holds a
+ * single lattice (FP32: up to 64 nodes wide and 256 high, or 128 x 128; FP64:
+ * up to 64 x 128; the last strip of 16 (FP32 up to 64 wide) or 8 rows at
+ * least 2 rows high) in the shared memory of one thread-block cluster of up
+ * to 16 CTAs for all n steps of an lbm_step call: one launch, strips of rows
+ * per CTA, edge rows exchanged through distributed shared memory and one
+ * cluster barrier per step (the tile configuration is ignored; LBM_EINVAL
+ * for a batch, a lattice outside those sizes, or a device that cannot hold
+ * the cluster).  Every schedule gives the same bits. */
 int lbm_set_schedule(lbm_ctx* ctx, int tile_config, int schedule);
 /* Time every (tile configuration, schedule) pair over `steps` steps of the
  * current state (which is restored afterwards) and keep the fastest (one

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # the step kernel writes every fused multiply-add explicitly (fma()); no
 # implicit contraction, so its rounding does not depend on the instantiation
-PER_FILE_FLAGS = {f: ["-fmad=false"] for f in ("lbm_step.cu", "lbm_step_f32.cu", "lbm_step_f64.cu")}
+PER_FILE_FLAGS = {f: ["-fmad=false"] for f in ("lbm_step.cu", "lbm_step_f32.cu", "lbm_step_f64.cu", "lbm_cluster.cu")}
 
 
 def nvcc() -> str:

@@ -567,6 +567,8 @@ cudaError_t launch_step(lbm_ctx* c, int parity) {
 int apply_schedule(lbm_ctx* c, int cfg, int sched) {
     if (sched == 3 && !lbm::run_supported(c->prec, cfg))
         return fail(c, LBM_EINVAL, "the multi-step schedule needs a tile configuration of one box per CTA%s");
+    if (sched == 4 && (c->n != 1 || !lbm::cluster_supported(c->prec, c->nx[0], c->ny[0])))
+        return fail(c, LBM_EINVAL, "the cluster schedule needs one lattice that fits one cluster's shared memory%s");
     c->cfg = cfg;
     c->sched = sched;
     drop_graphs(c);
@@ -639,8 +641,21 @@ int sync_all(lbm_ctx* c) {
     return LBM_OK;
 }
 
+// n steps of a lattice held in one cluster's shared memory (schedule 4):
+// one launch, then the ghost cells of the time level it wrote last.
+int cluster_steps(lbm_ctx* c, int n) {
+    if (n <= 0) return LBM_OK;
+    CK(c, lbm::cluster_run(c->h[0], c->parity, n, c->stream));
+    CK(c, lbm::aux_fill_ghosts(c->h[0], c->d_inst, c->parity ^ (n & 1), c->stream));
+    c->parity ^= (n & 1);
+    c->steps += n;
+    c->launches += 1;
+    return LBM_OK;
+}
+
 int launch_steps(lbm_ctx* c, int n) {
     if (c->sched == 3) return run_steps(c, n);
+    if (c->sched == 4) return cluster_steps(c, n);
     for (int k = 0; k < n; ++k) {
         CK(c, launch_step(c, c->parity));
         c->parity ^= 1;
@@ -1007,7 +1022,7 @@ int lbm_init_density(lbm_ctx* c, const double* rho, const double* ux, const doub
 // step as a plain launch; every graph has an even number of steps, so the
 // parity a replay starts from is the current one.
 int step_n(lbm_ctx* c, int n) {
-    if (c->use_graphs && c->sched != 3) {
+    if (c->use_graphs && c->sched < 3) {
         for (int level = kGraphLevels - 1; level >= 0; --level) {
             const int len = 2 << level;
             while (n >= len && (level == kGraphLevels - 1 || n < 2 * len)) {
@@ -1330,11 +1345,13 @@ int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double*
     int bc = c->cfg, bs = c->sched;
     for (int k = 0; k < lbm::step_config_count(c->prec); ++k)
         for (int s = 0; s < lbm::kMaxSched; ++s) {
-            // one lattice: the one-step launch (0) or the multi-step one (3)
-            if ((c->n == 1 && s != 0 && s != 3) || (s == 3 && !lbm::run_supported(c->prec, k))) continue;
+            // one lattice: the one-step launch (0), the multi-step one (3) or
+            // the cluster (4, one tile configuration stands for all)
+            if ((c->n == 1 && s != 0 && s < 3) || (s == 3 && !lbm::run_supported(c->prec, k))) continue;
+            if (s == 4 && (k > 0 || c->n != 1 || !lbm::cluster_supported(c->prec, c->nx[0], c->ny[0]))) continue;
             rc = apply_schedule(c, k, s);
             if (rc) break;
-            rc = step_n(c, c->use_graphs && s != 3 ? kGraphSteps : 2);
+            rc = step_n(c, c->use_graphs && s < 3 ? kGraphSteps : 2);
             if (rc) break;
             CK(c, cudaEventRecord(e0, c->stream));
             rc = step_n(c, steps);
@@ -1372,7 +1389,7 @@ int lbm_use_graphs(lbm_ctx* c, int on) {
 
 int lbm_capture_graphs(lbm_ctx* c) {
     if (!c) return LBM_EINVAL;
-    if (!c->use_graphs || c->sched == 3) return LBM_OK;
+    if (!c->use_graphs || c->sched >= 3) return LBM_OK;
     int rc = ready(c);
     if (rc) return rc;
     CK(c, cudaSetDevice(c->device));

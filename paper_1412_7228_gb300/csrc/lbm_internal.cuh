@@ -22,7 +22,7 @@
 namespace lbm {
 
 constexpr int GY = 2;          // ghost rows per side
-constexpr int kMaxSched = 4;   // CTA schedules known to lbm_set_schedule (3: multi-step persistent)
+constexpr int kMaxSched = 5;   // CTA schedules known to lbm_set_schedule (3: multi-step persistent, 4: cluster)
 
 template <typename T> struct Prec;
 template <> struct Prec<float> { static constexpr int GX = 8; static constexpr int HX = 4; };
@@ -339,6 +339,13 @@ cudaError_t step_launch(int prec, int k, const Inst* d_insts, const void* args, 
 bool run_supported(int prec, int k);
 cudaError_t run_launch(int prec, int k, const Inst* d_insts, const void* args, bool one, int ntiles, int nsteps,
                        unsigned long long timeout_ns, cudaStream_t st);
+
+// One lattice held in the shared memory of a thread-block cluster for n
+// steps (lbm_cluster.cu; schedule 4): whether this device can run it for an
+// nx x ny lattice of precision prec, and the launch (host: the descriptor;
+// the caller refills the ghost cells of the time level written last).
+bool cluster_supported(int prec, int nx, int ny);
+cudaError_t cluster_run(const Inst& host, int parity, int nsteps, cudaStream_t st);
 
 // Auxiliary kernels (lbm_aux.cu); `host` is the host copy of the descriptor.
 cudaError_t aux_init(const Inst& host, const Inst* d_inst, const double* rho, const double* ux,

@@ -141,6 +141,57 @@ def test_graph_replays_of_every_length_give_the_one_step_bits(P):
     lat.close()
 
 
+def test_cluster_schedule_gives_the_one_step_bits(P):
+    """Schedule 4 holds a single lattice in the shared memory of one
+    thread-block cluster (strips of rows per CTA, edge rows exchanged through
+    distributed shared memory, one cluster barrier per step): the one-step
+    bits for lattices of one CTA up to sixteen, ragged last strips, the fast
+    and the general path, however the steps are split into calls; refused
+    for a batch and for lattices it cannot hold."""
+    eos, op, rg, rl = cs_case(P)
+    shapes = {P.LBM_FP32: [(64, 64), (100, 100), (128, 128), (90, 75), (33, 18), (8, 5), (50, 2)],
+              P.LBM_FP64: [(64, 64), (40, 30), (8, 5), (50, 100)]}
+    for prec, cases in shapes.items():
+        for nx, ny in cases:
+            rho0 = I.droplet_density(nx, ny, min(nx, ny) / 4, rl, rg)
+            base = gpu_run(P, prec, eos, op, rho0, 37, rho_ref=rg)
+            lat = P.Lattice(nx, ny, prec)
+            lat.set_schedule(0, 4)
+            lat.set_params(eos, op.A, op.kappa, G=op.G, s=op.s, rho_ref=rg)
+            lat.init_density(rho0)
+            lat.use_graphs(True)
+            n0 = lat.kernel_launches
+            for n in (1, 0, 7, 29):
+                lat.step(n)
+            assert lat.kernel_launches - n0 == 3 and lat.steps_done == 37
+            lat.sync()
+            assert np.array_equal(lat.read_populations(), base), (prec, nx, ny)
+            assert np.array_equal(lat.read_fields(which=("rho",))["rho"],
+                                  gpu_fields(P, prec, eos, op, rho0, 37, rg)), (prec, nx, ny)
+            lat.close()
+    for prec, (nx, ny) in ((P.LBM_FP32, (200, 50)), (P.LBM_FP32, (64, 17)), (P.LBM_FP64, (100, 40))):
+        lat = P.Lattice(nx, ny, prec)
+        with pytest.raises(P.LbmError) as ei:
+            lat.set_schedule(0, 4)
+        assert ei.value.code == -1
+        lat.close()
+    b = P.Batch([32, 32], [32, 32], P.LBM_FP32)
+    with pytest.raises(P.LbmError):
+        b.set_schedule(0, 4)
+    b.close()
+
+
+def gpu_fields(P, prec, eos, op, rho0, steps, rho_ref):
+    ny, nx = rho0.shape
+    lat = P.Lattice(nx, ny, prec)
+    lat.set_params(eos, op.A, op.kappa, G=op.G, s=op.s, rho_ref=rho_ref)
+    lat.init_density(rho0)
+    lat.step(steps)
+    rho = lat.read_fields(which=("rho",))["rho"]
+    lat.close()
+    return rho
+
+
 def test_multi_step_launch_in_pieces_and_tiny_lattices(P):
     """The multi-step schedule gives the one-step bits however the steps are
     split into calls (odd counts flip the time level inside a launch), on a

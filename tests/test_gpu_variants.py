@@ -121,8 +121,8 @@ def test_every_variant_gives_the_same_bits_in_every_schedule(P, prec):
     """The variants take the general path or other pressure laws in the
     fused kernels: the Peng-Robinson and van der Waals laws, the
     density-dependent viscosity, Li's source entry and G = 0.  One step per
-    launch and the multi-step schedule, on tile shapes that do not divide the
-    lattice, give the same bits for each."""
+    launch, the multi-step schedule and the cluster schedule, on tile shapes
+    that do not divide the lattice, give the same bits for each."""
     from paper_1412_7228_gb300 import experiments as E
     eos_pr, op_pr = _pr(P)
     vdw = E.vdw_eos(0.9, 0.3)
@@ -146,3 +146,8 @@ def test_every_variant_gives_the_same_bits_in_every_schedule(P, prec):
         other = [k for k, c in enumerate(P.lbm_tile_configs(prec)) if c[3] == 1][-1]
         assert np.array_equal(_run(P, prec, eos, op, rho0, 23, rho_ref, visc, sched=3, tile=other), base), \
             (op.eos, visc, other)
+        # the cluster schedule, on a 64 x 60 window around the lattice's centre
+        # (the drop or ellipse whole inside, gas or liquid at its edges)
+        w = np.ascontiguousarray(rho0[5:65, 43:107])
+        ref = _run(P, prec, eos, op, w, 23, rho_ref, visc)
+        assert np.array_equal(_run(P, prec, eos, op, w, 23, rho_ref, visc, sched=4), ref), (op.eos, visc, 4)
