@@ -354,6 +354,33 @@ def test_batch_of_more_than_64_instances(P):
             assert np.array_equal(outs[i], solo[i]), (cfg, sched, i)
 
 
+def test_multi_step_chunks_of_mixed_sizes_give_the_solo_bits(P):
+    """The multi-step schedule's chunking on a batch of mixed sizes: a lattice
+    whose populations exceed a chunk's budget (a chunk of its own), lattices
+    sorted largest first and spread over even chunks, and thin ones (one
+    tile column; a last tile row one node high): every instance gets the
+    bits it gets alone."""
+    eos, op, rg, rl = cs_case(P)
+    shapes = [(64, 64), (2100, 2100), (300, 20), (17, 1000), (64, 64), (900, 700), (1000, 17), (64, 64)]
+    rhos = [I.spinodal_density(nx, ny, rho0=0.25, amp=0.01, seed=nx * 7 + ny) for nx, ny in shapes]
+    steps = 12
+    solo = [gpu_run(P, P.LBM_FP32, eos, op, r, steps, rho_ref=0.25) for r in rhos]
+    b = P.Batch([s_[0] for s_ in shapes], [s_[1] for s_ in shapes], P.LBM_FP32)
+    b.set_schedule(0, 3)
+    for i, r in enumerate(rhos):
+        b.set_params(i, eos, op.A, op.kappa, s=S_CFG, rho_ref=0.25)
+        b.init_density(i, r)
+    n0 = b.kernel_launches
+    b.step(5)
+    b.step(7)
+    launches = b.kernel_launches - n0
+    outs = [b.read_populations(i) for i in range(len(shapes))]
+    b.close()
+    assert launches % 2 == 0 and 2 * 2 <= launches <= 2 * len(shapes)   # the same chunks for both calls
+    for i in range(len(shapes)):
+        assert np.array_equal(outs[i], solo[i]), (i, shapes[i])
+
+
 def test_checkpoint_resume_is_bit_identical(P, tmp_path):
     eos, op, rg, rl = cs_case(P)
     rho0 = I.droplet_density(70, 50, 12, rl, rg)
