@@ -593,8 +593,11 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers -------------
     e2e = None
     if not args.no_e2e:
-        host_rho = torch.from_numpy(rho0).pin_memory().numpy()
-        out_rho = torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy()
+        # fields in the lattice's precision: FP32 lattices take and return float32
+        # (lbm_init_density_f32 / lbm_read_fields_f32), FP64 ones float64
+        fdt = np.float32 if prec == P.LBM_FP32 else np.float64
+        host_rho = torch.from_numpy(rho0.astype(fdt)).pin_memory().numpy()
+        out_rho = torch.empty((ny, nx), dtype=torch.float32 if fdt == np.float32 else torch.float64).pin_memory().numpy()
         eos = P.Eos(kind=P.LBM_EOS_CS, a=1.0, b=4.0, R=1.0, K=1.0)
         _, Tc, _ = P.lbm_eos_critical(eos)
         eos.T = TR_CFG * Tc
@@ -610,12 +613,14 @@ def run_ours(args):
         t0 = time.perf_counter()
         lat.init_density(host_rho)
         lat.step(args.steps)
-        lat.read_fields(which=("rho",), out={"rho": out_rho})
+        lat.read_fields(which=("rho",), out={"rho": out_rho}, dtype=fdt)
         t_e2e = time.perf_counter() - t0
         lat.close()
+        esz = np.dtype(fdt).itemsize
         e2e = {"value": N * args.steps / t_e2e / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": 8 * N / args.steps, "d2h_bytes_per_step": 8 * N / args.steps,
-               "what": "lbm_init_density from pinned host rho, lbm_step(K), lbm_read_fields(rho) to host"}
+               "h2d_bytes_per_step": esz * N / args.steps, "d2h_bytes_per_step": esz * N / args.steps,
+               "what": "lbm_init_density%s from pinned host rho, lbm_step(K), lbm_read_fields%s(rho) to pinned host memory"
+                       % (("_f32", "_f32") if esz == 4 else ("", ""))}
 
     # ---- the plain-method workload in full: 64^2 droplet, 10^4 steps --------
     plain = None

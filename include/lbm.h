@@ -175,6 +175,11 @@ int lbm_batch_set_viscosity(lbm_ctx* ctx, int i, int enable, double nu_gas, doub
 int lbm_init_density(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
 int lbm_batch_init_density(lbm_ctx* ctx, int i, const double* rho, const double* ux,
                            const double* uy);
+/* The same from fields of nx*ny floats (half the bytes to move): each value
+ * is widened to FP64 exactly, then as above. */
+int lbm_init_density_f32(lbm_ctx* ctx, const float* rho, const float* ux, const float* uy);
+int lbm_batch_init_density_f32(lbm_ctx* ctx, int i, const float* rho, const float* ux,
+                               const float* uy);
 
 /* Enqueue n time steps (Eqs. 1, 9, 10, 23, 25, 26: density and psi, hybrid
  * force, modifying tensor, moment-space collision, streaming) of every
@@ -195,6 +200,10 @@ int lbm_clear_status(lbm_ctx* ctx);
 int lbm_read_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* psi);
 int lbm_batch_read_fields(lbm_ctx* ctx, int i, double* rho, double* ux, double* uy,
                           double* psi);
+/* The same into fields of nx*ny floats (half the bytes to move): each value
+ * is the FP64 result rounded to the nearest float. */
+int lbm_read_fields_f32(lbm_ctx* ctx, float* rho, float* ux, float* uy, float* psi);
+int lbm_batch_read_fields_f32(lbm_ctx* ctx, int i, float* rho, float* ux, float* uy, float* psi);
 
 /* Pre-collision populations f_a(x, t) as 9*nx*ny doubles, index a*nx*ny + y*nx + x. */
 int lbm_read_populations(lbm_ctx* ctx, double* f);

@@ -36,15 +36,15 @@ template <typename T> __device__ __forceinline__ long long at(const Inst* I, int
 // by the weights in FP32 (within 1.5 ulp of the correctly rounded value, and
 // two FP64 operations per node instead of seven: GB300's FP64 pipe would
 // otherwise bound the initialisation).
-template <typename T, bool REST>
-__global__ void k_init(const Inst* __restrict__ I, const double* __restrict__ rho, const double* __restrict__ ux,
-                       const double* __restrict__ uy, int parity) {
+template <typename T, bool REST, typename R>
+__global__ void k_init(const Inst* __restrict__ I, const R* __restrict__ rho, const R* __restrict__ ux,
+                       const R* __restrict__ uy, int parity) {
     const int nx = I->nx, ny = I->ny;
     T* p = popk<T>(I, parity);
     const double rr = static_cast<double>(phys<T>(I).rho_ref);
     LBM_FOR_NODES(nx, ny) {
         const long long i = static_cast<long long>(y) * nx + x;
-        const double r = rho[i], u = !REST && ux ? ux[i] : 0.0, v = !REST && uy ? uy[i] : 0.0;
+        const double r = rho[i], u = !REST && ux ? double(ux[i]) : 0.0, v = !REST && uy ? double(uy[i]) : 0.0;
         const double u2 = u * u + v * v;
         // at rest: the three weights' products
         const double d = r - rr;
@@ -75,22 +75,28 @@ __global__ void k_init(const Inst* __restrict__ I, const double* __restrict__ rh
 // The checks of an initial field, on the device: bit 1 of *bad when a
 // density is not finite, not positive or not below rho_max, bit 2 when a
 // velocity is not finite (the caller has zeroed *bad).
-__global__ void k_check_init(const double* __restrict__ rho, const double* __restrict__ ux,
-                             const double* __restrict__ uy, long long N, double rho_max, int* bad) {
+// Bit patterns of the field's type as signed integers, and the exponent field.
+__device__ __forceinline__ long long bits_of(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ long long bits_of(float v) { return __float_as_int(v); }
+template <typename R> __host__ __device__ constexpr long long exp_mask() {
+    return sizeof(R) == 8 ? 0x7ff0000000000000ll : 0x7f800000ll;
+}
+template <typename R>
+__global__ void k_check_init(const R* __restrict__ rho, const R* __restrict__ ux, const R* __restrict__ uy,
+                             long long N, double rho_max, int* bad) {
     // on the bit patterns, as integers (no FP64 work): for rho_max > 0,
-    // 0 < r < rho_max with r finite is 0 < bits(r) < bits(rho_max) (positive
-    // doubles order as their patterns; negatives and -0 have the sign bit,
-    // NaN and inf patterns lie above every finite value); finite is an
-    // exponent field below all ones
-    const long long top = __double_as_longlong(rho_max);
-    constexpr unsigned long long kExp = 0x7ff0000000000000ull;
-    auto finite = [](double v) {
-        return (static_cast<unsigned long long>(__double_as_longlong(v)) & kExp) != kExp;
-    };
+    // 0 < r < rho_max with r finite is 0 < bits(r) < bits(top), top = rho_max
+    // in FP64, or for FP32 fields the smallest float not below rho_max
+    // (positive values order as their patterns; negatives and -0 have the
+    // sign bit, NaN and inf patterns lie above every finite value); finite is
+    // an exponent field below all ones
+    const long long top = sizeof(R) == 8 ? bits_of(rho_max) : bits_of(__double2float_ru(rho_max));
+    constexpr long long kExp = exp_mask<R>();
+    auto finite = [](R v) { return (bits_of(v) & kExp) != kExp; };
     int b = 0;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long r = __double_as_longlong(rho[i]);
+        const long long r = bits_of(rho[i]);
         if (!(r > 0 && r < top)) b |= 1;
         if ((ux && !finite(ux[i])) || (uy && !finite(uy[i]))) b |= 2;
     }
@@ -215,8 +221,8 @@ __device__ void node_fields(const Inst* I, const T* p, int x, int y, double* rho
 // One macroscopic field per launch (0 rho, 1 u_x, 2 u_y, 3 psi), each its
 // own kernel: the density read-back keeps the registers of a plain gather.
 // Rows [y0, y1) of the field, at their place in out (row-major nx x ny).
-template <typename T, int FIELD>
-__global__ void k_field(const Inst* __restrict__ I, int parity, int y0, int y1, double* __restrict__ out) {
+template <typename T, int FIELD, typename O>
+__global__ void k_field(const Inst* __restrict__ I, int parity, int y0, int y1, O* __restrict__ out) {
     const int nx = I->nx;
     const T* p = popk<T>(I, parity);
     for (int y = y0 + static_cast<int>(blockIdx.y); y < y1; y += gridDim.y)
@@ -234,7 +240,7 @@ __global__ void k_field(const Inst* __restrict__ I, int parity, int y0, int y1, 
                 node_fields<T>(I, p, x, y, &r, &u, &w, &s);
                 v = FIELD == 1 ? u : w;
             }
-            out[i] = v;
+            out[i] = static_cast<O>(v);
         }
 }
 
@@ -439,22 +445,39 @@ cudaError_t aux_fp64_fma_rate(int iters, cudaStream_t st, double* flops_per_s, d
     return cudaSuccess;
 }
 
-cudaError_t aux_init(const Inst& h, const Inst* d, const double* rho, const double* ux, const double* uy,
-                     int parity, cudaStream_t st) {
+template <typename R>
+cudaError_t init_t(const Inst& h, const Inst* d, const R* rho, const R* ux, const R* uy, int parity,
+                   cudaStream_t st) {
     const dim3 g = grid_2d(h.nx, h.ny);
     const bool rest = !ux && !uy;
-    if (h.prec == LBM_FP32 && rest) k_init<float, true><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
-    else if (h.prec == LBM_FP32) k_init<float, false><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
-    else if (rest) k_init<double, true><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
-    else k_init<double, false><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    if (h.prec == LBM_FP32 && rest) k_init<float, true, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    else if (h.prec == LBM_FP32) k_init<float, false, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    else if (rest) k_init<double, true, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
+    else k_init<double, false, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return aux_fill_ghosts(h, d, parity, st);
 }
 
-cudaError_t aux_check_init(const double* rho, const double* ux, const double* uy, long long N, double rho_max,
+cudaError_t aux_init(const Inst& h, const Inst* d, const void* rho, const void* ux, const void* uy, bool f32,
+                     int parity, cudaStream_t st) {
+    if (f32)
+        return init_t(h, d, static_cast<const float*>(rho), static_cast<const float*>(ux),
+                      static_cast<const float*>(uy), parity, st);
+    return init_t(h, d, static_cast<const double*>(rho), static_cast<const double*>(ux),
+                  static_cast<const double*>(uy), parity, st);
+}
+
+cudaError_t aux_check_init(const void* rho, const void* ux, const void* uy, bool f32, long long N, double rho_max,
                            int* bad, cudaStream_t st) {
-    k_check_init<<<grid_for(N), kThreads, 0, st>>>(rho, ux, uy, N, rho_max, bad);
+    if (f32)
+        k_check_init<float><<<grid_for(N), kThreads, 0, st>>>(static_cast<const float*>(rho),
+                                                               static_cast<const float*>(ux),
+                                                               static_cast<const float*>(uy), N, rho_max, bad);
+    else
+        k_check_init<double><<<grid_for(N), kThreads, 0, st>>>(static_cast<const double*>(rho),
+                                                                static_cast<const double*>(ux),
+                                                                static_cast<const double*>(uy), N, rho_max, bad);
     return cudaGetLastError();
 }
 
@@ -475,18 +498,24 @@ cudaError_t aux_gather_plane(const Inst& h, const Inst* d, int parity, int a, do
     return cudaGetLastError();
 }
 
-cudaError_t aux_field(const Inst& h, const Inst* d, int parity, int field, int y0, int y1, double* out,
-                      cudaStream_t st) {
+template <typename O>
+cudaError_t field_t(const Inst& h, const Inst* d, int parity, int field, int y0, int y1, O* out, cudaStream_t st) {
     const dim3 g = grid_2d(h.nx, y1 - y0);
     auto go = [&](auto k) { k<<<g, kThreads, 0, st>>>(d, parity, y0, y1, out); };
     const bool f32 = h.prec == LBM_FP32;
     switch (field) {
-    case 0: f32 ? go(k_field<float, 0>) : go(k_field<double, 0>); break;
-    case 1: f32 ? go(k_field<float, 1>) : go(k_field<double, 1>); break;
-    case 2: f32 ? go(k_field<float, 2>) : go(k_field<double, 2>); break;
-    default: f32 ? go(k_field<float, 3>) : go(k_field<double, 3>); break;
+    case 0: f32 ? go(k_field<float, 0, O>) : go(k_field<double, 0, O>); break;
+    case 1: f32 ? go(k_field<float, 1, O>) : go(k_field<double, 1, O>); break;
+    case 2: f32 ? go(k_field<float, 2, O>) : go(k_field<double, 2, O>); break;
+    default: f32 ? go(k_field<float, 3, O>) : go(k_field<double, 3, O>); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t aux_field(const Inst& h, const Inst* d, int parity, int field, int y0, int y1, void* out, bool f32out,
+                      cudaStream_t st) {
+    if (f32out) return field_t(h, d, parity, field, y0, y1, static_cast<float*>(out), st);
+    return field_t(h, d, parity, field, y0, y1, static_cast<double*>(out), st);
 }
 
 cudaError_t aux_measure(const Inst& h, const Inst* d, int parity, double cxc, double cyc, double r_in,

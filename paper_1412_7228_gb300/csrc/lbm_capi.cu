@@ -704,6 +704,101 @@ int valid_params(const lbm_eos* eos, double A, double kappa, double G, const dou
 }  // namespace
 
 // =========================================================================
+namespace {
+// Initial state from host fields of R (double, or float widened exactly).
+template <typename R> int init_density_t(lbm_ctx* c, int i, const R* rho, const R* ux, const R* uy) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!rho) return fail(c, LBM_EINVAL, "rho must not be NULL%s");
+    if (!c->hp[i].set) return fail(c, LBM_EINVAL, "set the parameters before the density%s");
+    Range range("lbm_batch_init_density");
+    const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
+    // the EOS range only matters when psi is evaluated (G != 0)
+    const double rmax = c->hp[i].G != 0.0 ? eos_rho_max(c->hp[i].eos) : HUGE_VAL;
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaStreamSynchronize(c->stream));
+    R* const scratch = reinterpret_cast<R*>(c->d_scratch);
+    R* d_rho = scratch;
+    R* d_ux = ux ? scratch + N : nullptr;
+    R* d_uy = uy ? scratch + 2 * N : nullptr;
+    constexpr bool f32 = sizeof(R) == 4;
+    CK(c, cudaMemcpyAsync(d_rho, rho, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+    if (ux) CK(c, cudaMemcpyAsync(d_ux, ux, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+    if (uy) CK(c, cudaMemcpyAsync(d_uy, uy, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+    // the field is checked on the device before anything of the instance is written
+    int* d_bad = reinterpret_cast<int*>(c->d_result);
+    int bad = 0;
+    CK(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+    CK(c, lbm::aux_check_init(d_rho, d_ux, d_uy, f32, static_cast<long long>(N), rmax, d_bad, c->stream));
+    CK(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (bad & 1) return fail(c, LBM_EINVAL, "initial density must be finite, positive and inside the EOS range%s");
+    if (bad & 2) return fail(c, LBM_EINVAL, "initial velocity must be finite%s");
+    CK(c, lbm::aux_init(c->h[i], c->d_inst + i, d_rho, d_ux, d_uy, f32, c->parity, c->stream));
+    CK(c, cudaMemsetAsync(c->d_status + i, 0, sizeof(int), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->inited[i] = 1;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+// Macroscopic fields into host arrays of O (double, or float: each value
+// rounded to nearest).
+template <typename O> int read_fields_t(lbm_ctx* c, int i, O* rho, O* ux, O* uy, O* psi) {
+    int rc = check_idx(c, i);
+    if (rc) return rc;
+    if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
+    Range range("lbm_batch_read_fields");
+    CK(c, cudaSetDevice(c->device));
+    const int nx = c->nx[i], ny = c->ny[i];
+    const size_t N = static_cast<size_t>(nx) * ny;
+    // a large lattice in row bands: band b's copy to the host overlaps band b + 1's kernel
+    const int bands = N >= kReadBandMin && ny >= kReadBands ? kReadBands : 1;
+    if (bands > 1 && !c->copy_stream) {   // created once, whole or not at all
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev[kReadBands] = {};
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int b = 0; b < kReadBands && e == cudaSuccess; ++b)
+            e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (auto x : ev)
+                if (x) cudaEventDestroy(x);
+            if (cs) cudaStreamDestroy(cs);
+            return cuda_fail(c, e, "read-back copy stream");
+        }
+        c->copy_stream = cs;
+        std::copy(ev, ev + kReadBands, c->band_done);
+    }
+    O* outs[4] = {rho, ux, uy, psi};
+    O* const scratch = reinterpret_cast<O*>(c->d_scratch);
+    constexpr bool f32 = sizeof(O) == 4;
+    for (int f = 0; f < 4; ++f) {
+        if (!outs[f]) continue;
+        if (bands == 1) {
+            CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, 0, ny, scratch, f32, c->stream));
+            CK(c, cudaMemcpyAsync(outs[f], scratch, N * sizeof(O), cudaMemcpyDeviceToHost, c->stream));
+            CK(c, cudaStreamSynchronize(c->stream));
+            continue;
+        }
+        for (int b = 0; b < bands; ++b) {
+            const int y0 = static_cast<int>(static_cast<long long>(ny) * b / bands);
+            const int y1 = static_cast<int>(static_cast<long long>(ny) * (b + 1) / bands);
+            const size_t off = static_cast<size_t>(y0) * nx, cnt = static_cast<size_t>(y1 - y0) * nx;
+            CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, y0, y1, scratch, f32, c->stream));
+            CK(c, cudaEventRecord(c->band_done[b], c->stream));
+            CK(c, cudaStreamWaitEvent(c->copy_stream, c->band_done[b], 0));
+            CK(c, cudaMemcpyAsync(outs[f] + off, scratch + off, cnt * sizeof(O), cudaMemcpyDeviceToHost,
+                                  c->copy_stream));
+        }
+        CK(c, cudaStreamSynchronize(c->copy_stream));   // before the next field reuses the scratch
+    }
+    int code = LBM_OK;
+    rc = status_of(c, i, &code);
+    return rc ? rc : code;
+}
+
+}  // namespace
+
 extern "C" {
 
 int lbm_eos_pressure(const lbm_eos* eos, double rho, double* p) {
@@ -978,42 +1073,18 @@ int lbm_set_viscosity(lbm_ctx* c, int enable, double nu_gas, double nu_liquid, d
     return lbm_batch_set_viscosity(c, 0, enable, nu_gas, nu_liquid, rho_gas, rho_liquid);
 }
 
-int lbm_batch_init_density(lbm_ctx* c, int i, const double* rho, const double* ux, const double* uy) {
-    int rc = check_idx(c, i);
-    if (rc) return rc;
-    if (!rho) return fail(c, LBM_EINVAL, "rho must not be NULL%s");
-    if (!c->hp[i].set) return fail(c, LBM_EINVAL, "set the parameters before the density%s");
-    Range range("lbm_batch_init_density");
-    const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
-    // the EOS range only matters when psi is evaluated (G != 0)
-    const double rmax = c->hp[i].G != 0.0 ? eos_rho_max(c->hp[i].eos) : HUGE_VAL;
-    CK(c, cudaSetDevice(c->device));
-    CK(c, cudaStreamSynchronize(c->stream));
-    double* d_rho = c->d_scratch;
-    double* d_ux = ux ? c->d_scratch + N : nullptr;
-    double* d_uy = uy ? c->d_scratch + 2 * N : nullptr;
-    CK(c, cudaMemcpyAsync(d_rho, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (ux) CK(c, cudaMemcpyAsync(d_ux, ux, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (uy) CK(c, cudaMemcpyAsync(d_uy, uy, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    // the field is checked on the device before anything of the instance is written
-    int* d_bad = reinterpret_cast<int*>(c->d_result);
-    int bad = 0;
-    CK(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
-    CK(c, lbm::aux_check_init(d_rho, d_ux, d_uy, static_cast<long long>(N), rmax, d_bad, c->stream));
-    CK(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    if (bad & 1) return fail(c, LBM_EINVAL, "initial density must be finite, positive and inside the EOS range%s");
-    if (bad & 2) return fail(c, LBM_EINVAL, "initial velocity must be finite%s");
-    CK(c, lbm::aux_init(c->h[i], c->d_inst + i, d_rho, d_ux, d_uy, c->parity, c->stream));
-    CK(c, cudaMemsetAsync(c->d_status + i, 0, sizeof(int), c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    c->inited[i] = 1;
-    c->steps = 0;
-    return LBM_OK;
-}
 
+int lbm_batch_init_density(lbm_ctx* c, int i, const double* rho, const double* ux, const double* uy) {
+    return init_density_t(c, i, rho, ux, uy);
+}
+int lbm_batch_init_density_f32(lbm_ctx* c, int i, const float* rho, const float* ux, const float* uy) {
+    return init_density_t(c, i, rho, ux, uy);
+}
 int lbm_init_density(lbm_ctx* c, const double* rho, const double* ux, const double* uy) {
-    return lbm_batch_init_density(c, 0, rho, ux, uy);
+    return init_density_t(c, 0, rho, ux, uy);
+}
+int lbm_init_density_f32(lbm_ctx* c, const float* rho, const float* ux, const float* uy) {
+    return init_density_t(c, 0, rho, ux, uy);
 }
 
 // n steps as lbm_step issues them.  With graphs on (one-step schedules):
@@ -1071,59 +1142,18 @@ int lbm_clear_status(lbm_ctx* c) {
     return LBM_OK;
 }
 
-int lbm_batch_read_fields(lbm_ctx* c, int i, double* rho, double* ux, double* uy, double* psi) {
-    int rc = check_idx(c, i);
-    if (rc) return rc;
-    if (!c->inited[i] || !c->hp[i].set) return fail(c, LBM_EINVAL, "instance not initialised%s");
-    Range range("lbm_batch_read_fields");
-    CK(c, cudaSetDevice(c->device));
-    const int nx = c->nx[i], ny = c->ny[i];
-    const size_t N = static_cast<size_t>(nx) * ny;
-    // a large lattice in row bands: band b's copy to the host overlaps band b + 1's kernel
-    const int bands = N >= kReadBandMin && ny >= kReadBands ? kReadBands : 1;
-    if (bands > 1 && !c->copy_stream) {   // created once, whole or not at all
-        cudaStream_t cs = nullptr;
-        cudaEvent_t ev[kReadBands] = {};
-        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-        for (int b = 0; b < kReadBands && e == cudaSuccess; ++b)
-            e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            for (auto x : ev)
-                if (x) cudaEventDestroy(x);
-            if (cs) cudaStreamDestroy(cs);
-            return cuda_fail(c, e, "read-back copy stream");
-        }
-        c->copy_stream = cs;
-        std::copy(ev, ev + kReadBands, c->band_done);
-    }
-    double* outs[4] = {rho, ux, uy, psi};
-    for (int f = 0; f < 4; ++f) {
-        if (!outs[f]) continue;
-        if (bands == 1) {
-            CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, 0, ny, c->d_scratch, c->stream));
-            CK(c, cudaMemcpyAsync(outs[f], c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-            CK(c, cudaStreamSynchronize(c->stream));
-            continue;
-        }
-        for (int b = 0; b < bands; ++b) {
-            const int y0 = static_cast<int>(static_cast<long long>(ny) * b / bands);
-            const int y1 = static_cast<int>(static_cast<long long>(ny) * (b + 1) / bands);
-            const size_t off = static_cast<size_t>(y0) * nx, cnt = static_cast<size_t>(y1 - y0) * nx;
-            CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, y0, y1, c->d_scratch, c->stream));
-            CK(c, cudaEventRecord(c->band_done[b], c->stream));
-            CK(c, cudaStreamWaitEvent(c->copy_stream, c->band_done[b], 0));
-            CK(c, cudaMemcpyAsync(outs[f] + off, c->d_scratch + off, cnt * sizeof(double), cudaMemcpyDeviceToHost,
-                                  c->copy_stream));
-        }
-        CK(c, cudaStreamSynchronize(c->copy_stream));   // before the next field reuses the scratch
-    }
-    int code = LBM_OK;
-    rc = status_of(c, i, &code);
-    return rc ? rc : code;
-}
 
+int lbm_batch_read_fields(lbm_ctx* c, int i, double* rho, double* ux, double* uy, double* psi) {
+    return read_fields_t(c, i, rho, ux, uy, psi);
+}
+int lbm_batch_read_fields_f32(lbm_ctx* c, int i, float* rho, float* ux, float* uy, float* psi) {
+    return read_fields_t(c, i, rho, ux, uy, psi);
+}
 int lbm_read_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* psi) {
-    return lbm_batch_read_fields(c, 0, rho, ux, uy, psi);
+    return read_fields_t(c, 0, rho, ux, uy, psi);
+}
+int lbm_read_fields_f32(lbm_ctx* c, float* rho, float* ux, float* uy, float* psi) {
+    return read_fields_t(c, 0, rho, ux, uy, psi);
 }
 
 int lbm_batch_read_populations(lbm_ctx* c, int i, double* f) {

@@ -348,18 +348,19 @@ bool cluster_supported(int prec, int nx, int ny);
 cudaError_t cluster_run(const Inst& host, int parity, int nsteps, cudaStream_t st);
 
 // Auxiliary kernels (lbm_aux.cu); `host` is the host copy of the descriptor.
-cudaError_t aux_init(const Inst& host, const Inst* d_inst, const double* rho, const double* ux,
-                     const double* uy, int parity, cudaStream_t st);
+// Fields of nx*ny doubles, or floats with f32 (each widened to FP64 exactly).
+cudaError_t aux_init(const Inst& host, const Inst* d_inst, const void* rho, const void* ux, const void* uy, bool f32,
+                     int parity, cudaStream_t st);
 cudaError_t aux_fill_ghosts(const Inst& host, const Inst* d_inst, int parity, cudaStream_t st);
 // bad |= 1: a density not finite, positive and below rho_max; |= 2: a velocity not finite
-cudaError_t aux_check_init(const double* rho, const double* ux, const double* uy, long long N, double rho_max,
+cudaError_t aux_check_init(const void* rho, const void* ux, const void* uy, bool f32, long long N, double rho_max,
                            int* bad, cudaStream_t st);
 cudaError_t aux_gather_plane(const Inst& host, const Inst* d_inst, int parity, int a, double* out,
                              cudaStream_t st);
 // field: 0 rho, 1 ux, 2 uy, 3 psi; rows [y0, y1), written at their place in
 // out (row-major, nx per row)
-cudaError_t aux_field(const Inst& host, const Inst* d_inst, int parity, int field, int y0, int y1, double* out,
-                      cudaStream_t st);
+cudaError_t aux_field(const Inst& host, const Inst* d_inst, int parity, int field, int y0, int y1, void* out,
+                      bool f32out, cudaStream_t st);   // f32out: floats, each the FP64 value rounded to nearest
 // out: 4 device words (see lbm_fp64_math_check); default stream.
 cudaError_t aux_math_check(long long n, double lo, double hi, unsigned long long* out);
 // FP64 FMA throughput of the current device (see lbm_fp64_fma_rate).

@@ -33,9 +33,10 @@ EXPORTS = [
     "lbm_fp64_fma_rate",
     "lbm_required_bytes", "lbm_batch_required_bytes", "lbm_create", "lbm_batch_create", "lbm_destroy",
     "lbm_set_params", "lbm_batch_set_params", "lbm_set_viscosity", "lbm_batch_set_viscosity",
-    "lbm_init_density", "lbm_batch_init_density",
+    "lbm_init_density", "lbm_batch_init_density", "lbm_init_density_f32", "lbm_batch_init_density_f32",
     "lbm_step", "lbm_sync", "lbm_status", "lbm_clear_status",
-    "lbm_read_fields", "lbm_batch_read_fields", "lbm_read_populations", "lbm_batch_read_populations",
+    "lbm_read_fields", "lbm_batch_read_fields", "lbm_read_fields_f32", "lbm_batch_read_fields_f32",
+    "lbm_read_populations", "lbm_batch_read_populations",
     "lbm_measure_pressure_jump", "lbm_batch_measure", "lbm_stats", "lbm_batch_stats",
     "lbm_save", "lbm_load", "lbm_tile_config_count", "lbm_tile_config", "lbm_set_schedule",
     "lbm_autotune", "lbm_use_graphs", "lbm_capture_graphs", "lbm_steps_done", "lbm_kernel_launches", "lbm_bytes_per_update",
@@ -111,12 +112,16 @@ def lib():
         "lbm_batch_set_viscosity": ([_vp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4, ctypes.c_int),
         "lbm_init_density": ([_vp, _dp, _dp, _dp], ctypes.c_int),
         "lbm_batch_init_density": ([_vp, ctypes.c_int, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_init_density_f32": ([_vp, _fp, _fp, _fp], ctypes.c_int),
+        "lbm_batch_init_density_f32": ([_vp, ctypes.c_int, _fp, _fp, _fp], ctypes.c_int),
         "lbm_step": ([_vp, ctypes.c_int], ctypes.c_int),
         "lbm_sync": ([_vp], ctypes.c_int),
         "lbm_status": ([_vp, ctypes.c_int], ctypes.c_int),
         "lbm_clear_status": ([_vp], ctypes.c_int),
         "lbm_read_fields": ([_vp, _dp, _dp, _dp, _dp], ctypes.c_int),
         "lbm_batch_read_fields": ([_vp, ctypes.c_int, _dp, _dp, _dp, _dp], ctypes.c_int),
+        "lbm_read_fields_f32": ([_vp, _fp, _fp, _fp, _fp], ctypes.c_int),
+        "lbm_batch_read_fields_f32": ([_vp, ctypes.c_int, _fp, _fp, _fp, _fp], ctypes.c_int),
         "lbm_read_populations": ([_vp, _dp], ctypes.c_int),
         "lbm_batch_read_populations": ([_vp, ctypes.c_int, _dp], ctypes.c_int),
         "lbm_measure_pressure_jump": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -166,6 +171,13 @@ def _ptr(a: Optional[np.ndarray]):
         return None
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(_dp)
+
+
+def _ptr32(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_fp)
 
 
 def _f64(a, shape):
@@ -328,7 +340,18 @@ class Batch:
         self._c(lib().lbm_batch_set_viscosity(self.ctx, i, int(enable), nu_gas, nu_liquid, rho_gas, rho_liquid))
 
     def init_density(self, i: int, rho, ux=None, uy=None):
+        """Initial state of instance i from (ny, nx) fields.  float32 arrays
+        (all of the given ones) go through the FP32 entry point, which moves
+        half the bytes; anything else is taken as float64."""
         shape = (self.ny[i], self.nx[i])
+        given = [a for a in (rho, ux, uy) if a is not None]
+        if all(isinstance(a, np.ndarray) and a.dtype == np.float32 for a in given):
+            r, u, v = (None if a is None else np.ascontiguousarray(a) for a in (rho, ux, uy))
+            for a in (r, u, v):
+                if a is not None and a.shape != shape:
+                    raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+            self._c(lib().lbm_batch_init_density_f32(self.ctx, i, _ptr32(r), _ptr32(u), _ptr32(v)))
+            return
         r, u, v = _f64(rho, shape), _f64(ux, shape), _f64(uy, shape)
         self._c(lib().lbm_batch_init_density(self.ctx, i, _ptr(r), _ptr(u), _ptr(v)))
 
@@ -344,20 +367,28 @@ class Batch:
     def clear_status(self):
         self._c(lib().lbm_clear_status(self.ctx))
 
-    def read_fields(self, i: int = 0, which=("rho", "ux", "uy", "psi"), out=None):
-        """Macroscopic fields of instance i as (ny, nx) float64 arrays.  `out`
-        may supply the destination arrays (e.g. in pinned memory, which the
-        device-to-host copy then fills directly)."""
+    def read_fields(self, i: int = 0, which=("rho", "ux", "uy", "psi"), out=None, dtype=np.float64):
+        """Macroscopic fields of instance i as (ny, nx) arrays of dtype
+        (float64, or float32: each value rounded to nearest, half the bytes to
+        move).  `out` may supply the destination arrays (e.g. in pinned
+        memory, which the device-to-host copy then fills directly)."""
+        dtype = np.dtype(dtype)
+        if dtype not in (np.dtype(np.float64), np.dtype(np.float32)):
+            raise ValueError("dtype must be float64 or float32")
         shape = (self.ny[i], self.nx[i])
         outs = {}
         for k in which:
             a = None if out is None else out.get(k)
             if a is None:
-                a = np.empty(shape)
-            elif a.shape != shape or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
-                raise ValueError("out[%r] must be a writeable C-contiguous float64 array of shape %s" % (k, shape))
+                a = np.empty(shape, dtype=dtype)
+            elif a.shape != shape or a.dtype != dtype or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+                raise ValueError("out[%r] must be a writeable C-contiguous %s array of shape %s" % (k, dtype, shape))
             outs[k] = a
-        self._c(lib().lbm_batch_read_fields(self.ctx, i, *[_ptr(outs.get(k)) for k in ("rho", "ux", "uy", "psi")]))
+        keys = ("rho", "ux", "uy", "psi")
+        if dtype == np.float32:
+            self._c(lib().lbm_batch_read_fields_f32(self.ctx, i, *[_ptr32(outs.get(k)) for k in keys]))
+        else:
+            self._c(lib().lbm_batch_read_fields(self.ctx, i, *[_ptr(outs.get(k)) for k in keys]))
         return outs
 
     def read_populations(self, i: int = 0) -> np.ndarray:

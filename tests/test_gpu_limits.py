@@ -173,6 +173,54 @@ def test_banded_read_back_of_a_large_lattice_matches_the_oracle_macro(P, prec):
     assert float(np.abs(got["ux"] - ux).max()) <= 1e-14 and float(np.abs(got["uy"] - uy).max()) <= 1e-14
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_fp32_field_interface(P, prec):
+    """The FP32 entry points move half the bytes and mean the same: a float32
+    initial field gives the populations of its exact float64 widening, every
+    float32 field read back is the float64 one rounded to nearest (banded
+    read-back of a lattice above 2^20 nodes included), and a float32 field
+    is checked like a float64 one (the EOS's upper limit is excluded; NaN,
+    non-positive densities and infinite velocities are refused and leave the
+    state as it was)."""
+    eos, op, rg, rl = _cs(P)
+    for nx, ny in ((48, 40), (1040, 1030)):
+        rho32 = I.droplet_density(nx, ny, min(nx, ny) / 4, rl, rg).astype(np.float32)
+        ux32 = (0.01 * np.sin(np.arange(nx * ny).reshape(ny, nx) * 0.01)).astype(np.float32)
+        a = P.Lattice(nx, ny, prec)
+        b = P.Lattice(nx, ny, prec)
+        for lat in (a, b):
+            lat.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=rg)
+        a.init_density(rho32, ux=ux32)
+        b.init_density(rho32.astype(np.float64), ux=ux32.astype(np.float64))
+        assert np.array_equal(a.read_populations(), b.read_populations())
+        a.step(4)
+        f64 = a.read_fields()
+        f32 = a.read_fields(dtype=np.float32)
+        for k in ("rho", "ux", "uy", "psi"):
+            assert f32[k].dtype == np.float32 and np.array_equal(f32[k], f64[k].astype(np.float32)), (nx, k)
+        a.close()
+        b.close()
+    lat = P.Lattice(48, 40, prec)
+    lat.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=rg)
+    good = I.droplet_density(48, 40, 10, rl, rg).astype(np.float32)
+    lat.init_density(good)
+    lat.step(3)
+    keep = lat.read_populations()
+    rmax = np.float32(4.0 / 4.0)   # Carnahan-Starling: 4/b
+    for field, ux in ((np.where(np.arange(48 * 40).reshape(40, 48) == 77, rmax, good), None),
+                      (np.where(np.arange(48 * 40).reshape(40, 48) == 5, np.float32(np.nan), good), None),
+                      (np.where(np.arange(48 * 40).reshape(40, 48) == 9, np.float32(-0.1), good), None),
+                      (good, np.where(np.arange(48 * 40).reshape(40, 48) == 3, np.float32(np.inf),
+                                      np.float32(0)).astype(np.float32))):
+        with pytest.raises(P.LbmError) as ei:
+            lat.init_density(field.astype(np.float32), ux=ux)
+        assert ei.value.code == -1
+        assert np.array_equal(lat.read_populations(), keep)
+    just_below = np.where(np.arange(48 * 40).reshape(40, 48) == 77, np.nextafter(rmax, np.float32(0)), good)
+    lat.init_density(just_below.astype(np.float32))
+    lat.close()
+
+
 def test_read_fields_into_caller_arrays(P):
     """read_fields fills caller-supplied (here pinned) arrays with the same
     values it returns in fresh ones, and rejects a wrong shape or dtype."""
