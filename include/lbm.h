@@ -184,8 +184,9 @@ int lbm_batch_init_density_f32(lbm_ctx* ctx, int i, const float* rho, const floa
 /* Enqueue n time steps (Eqs. 1, 9, 10, 23, 25, 26: density and psi, hybrid
  * force, modifying tensor, moment-space collision, streaming) of every
  * instance: one fused kernel launch per step (and per 64 instances),
- * replayed from a CUDA graph when graphs are on, or with schedule 3 one
- * launch per call (and per 32 instances).  Asynchronous. */
+ * replayed from CUDA graphs when graphs are on; with schedule 3 one launch
+ * per call and chunk of instances, with schedule 4 one launch per call.
+ * Asynchronous. */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* Wait for the stream; return the first sticky status of any instance. */
@@ -244,7 +245,9 @@ int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads, int* s
  * order, 1: the tiles of each launch's instances interleaved, 2: largest
  * instance first; a batch is stepped by one launch per 64 instances and
  * step).  Schedule 3 steps every instance through all n steps of an
- * lbm_step(n) call in one persistent launch per 32 instances: CTAs take
+ * lbm_step(n) call in one persistent launch per chunk of instances (up to 32
+ * instances and 80 MiB of populations, the instances taken largest first and
+ * spread evenly over as few chunks as that allows): CTAs take
  * (step, tile) items in step order from a counter in device memory and start
  * step s of a tile once every tile within two nodes of it (periodic) has
  * finished step s - 1 (each dependency wait bounded; one that gives up reports
