@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const __grid_constant__ Clust
     const T* fin = (a.nsteps & 1) ? box1 : box0;
     for (int e = tid; e < 9 * h * nx; e += NT) {
         const int x = e % nx, r = (e / nx) % h, q = e / (nx * h);
-        a.dst[q * a.plane + static_cast<long long>(y0 + r + GY) * a.pitch + (GXg + x)] = fin[q * PB + (GY + r) * WB + HX + x];
+        a.dst[q * a.plane + static_cast<long long>(y0 + r + GY) * a.pitch + (GXg + x)] =
+            fin[q * PB + (GY + r) * WB + HX + x];
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(a.status, ST_UNSTABLE);
 }
