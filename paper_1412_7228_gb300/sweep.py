@@ -310,11 +310,11 @@ def main(argv=None):
     ap.add_argument("--laplace", action="store_true", help="Laplace-law sweep (256^2, 5 radii x 4 kappa x 3 T)")
     ap.add_argument("--batched", action="store_true", help="64 uneven instances, batched vs sequential")
     ap.add_argument("--uniform", type=int, default=None, metavar="L",
-                    help="time --n droplets of L^2 (R0 = 0.2 L, 0.7 Tc, A = -0.85, kappa = 0.3) stepped together, "
-                         "with --tile/--schedule instead of autotuning and without graphs (one launch per step "
-                         "and 64 instances, as a profiler sees them)")
-    ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--schedule", type=int, default=0)
+                    help="time --n droplets of L^2 (R0 = 0.2 L, 0.7 Tc, A = -0.85, kappa = 0.3) stepped together: "
+                         "tile and schedule autotuned, graphs on; or with --tile/--schedule as given and without "
+                         "graphs (each launch as a profiler sees it)")
+    ap.add_argument("--tile", type=int, default=None)
+    ap.add_argument("--schedule", type=int, default=None)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--n", type=int, default=64)
@@ -331,11 +331,14 @@ def main(argv=None):
                "fits": [f.__dict__ for f in fits], "droplets": info.get("droplets")}
         print(json.dumps(out))
     if args.uniform:
-        steps = args.steps or 40
+        steps = args.steps or 2000
         drops = [Droplet(args.uniform, 0.2 * args.uniform, 0.7, -0.85, 0.3) for _ in range(args.n)]
-        r = run_batch(drops, steps, prec, graphs=False, schedule=(args.tile, args.schedule))
+        forced = args.tile is not None or args.schedule is not None
+        sched = (args.tile or 0, args.schedule or 0) if forced else None
+        r = run_batch(drops, steps, prec, graphs=not forced, schedule=sched)
+        tile, schedule = sched if forced else tuple(r["tune"][:2])
         print(json.dumps({"sweep": "uniform", "instances": args.n, "L": args.uniform, "steps": steps,
-                          "precision": args.precision, "tile": args.tile, "schedule": args.schedule,
+                          "precision": args.precision, "tile": tile, "schedule": schedule,
                           "seconds": r["seconds"], "mlups": r["mlups"], "launches": r["launches"],
                           "unstable": sum(d.status != 0 for d in drops)}))
     if args.batched:
