@@ -62,6 +62,7 @@ def slabs(eos: L.Eos, cases: Sequence[Tuple[float, float]], rho_l0: float, rho_g
         b.set_params(i, eos, A, k, G=-1.0, s=s, rho_ref=rho_g0)
         b.init_density(i, rho0)
     b.use_graphs(True)
+    b.autotune(40)   # tile and schedule: the same bits in every one
     b.step(steps)
     out = []
     for i in range(len(cases)):
@@ -80,6 +81,7 @@ def droplets(eos: L.Eos, cases: Sequence[Tuple[float, float, float]], L_: int, r
         b.set_params(i, eos, A, k, G=-1.0, s=s, rho_ref=rho_g0)
         b.init_density(i, I.droplet_density(L_, L_, R, rho_l0, rho_g0, width=width))
     b.use_graphs(True)
+    b.autotune(40)
     b.step(steps)
     out = []
     for i, (A, k, R) in enumerate(cases):
@@ -151,7 +153,8 @@ def oscillation(kappa: float, nu_l: float, nu_g: float = 0.2, L_: int = 120, rma
     lat.set_params(eos, A, kappa, G=-1.0, s=S_ONES, rho_ref=rg)
     lat.set_viscosity(nu_g, nu_l, rg, rl)
     lat.init_density(I.ellipse_density(L_, L_, rmax, rmin, rl, rg, width=4.0))
-    lat.use_graphs(every % 32 == 0)
+    lat.use_graphs(True)
+    lat.autotune(40)
     t, D = [], []
     for n in range(steps // every + 1):
         if n:
