@@ -105,3 +105,14 @@ def test_fp64_roofline_and_cpu_model_records(tmp_path):
     arm.write_text("processor\t: 0\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
     assert bench.cpu_model(str(x86)) == "Some CPU @ 2.0GHz"
     assert bench.cpu_model(str(arm)) == "Arm Neoverse V2 (part 0xd4f)"
+
+
+def test_graph_use_reports_the_replayed_steps():
+    """lbm_step(n) with graphs replays 32-, 16-, 8-, 4- and 2-step graphs for
+    every even part of n and launches an odd last step plainly; the bench line
+    reports that split."""
+    import bench
+    assert bench.graph_use(20) == {"graphs": True, "graph_steps": 20, "plain_launch_steps": 0}
+    assert bench.graph_use(2000) == {"graphs": True, "graph_steps": 2000, "plain_launch_steps": 0}
+    assert bench.graph_use(37) == {"graphs": True, "graph_steps": 36, "plain_launch_steps": 1}
+    assert bench.graph_use(1) == {"graphs": False, "graph_steps": 0, "plain_launch_steps": 1}
