@@ -87,3 +87,21 @@ def test_static_sampling_rejects_what_set_params_rejects(liblbm, bad):
     assert rc == P.lbm.LBM_EINVAL
     assert P.lib().lbm_eos_maxwell(ctypes.byref(eos.c()), out.ctypes.data_as(dp), out.ctypes.data_as(dp),
                                    out.ctypes.data_as(dp)) == P.lbm.LBM_EINVAL
+
+
+def test_context_calls_refuse_a_null_context(liblbm):
+    """Every call that takes a context returns LBM_EINVAL for NULL, before any
+    GPU work (so these run without a GPU)."""
+    import paper_1412_7228_gb300 as P
+    L = P.lib()
+    E = P.lbm.LBM_EINVAL
+    assert L.lbm_step(None, 1) == E
+    assert L.lbm_set_schedule(None, 0, 4) == E
+    assert L.lbm_use_graphs(None, 1) == E
+    assert L.lbm_capture_graphs(None) == E
+    assert L.lbm_init_density(None, None, None, None) == E
+    assert L.lbm_init_density_f32(None, None, None, None) == E
+    assert L.lbm_read_fields(None, None, None, None, None) == E
+    assert L.lbm_read_fields_f32(None, None, None, None, None) == E
+    assert L.lbm_batch_init_density_f32(None, 0, None, None, None) == E
+    assert L.lbm_batch_read_fields_f32(None, 0, None, None, None, None) == E
