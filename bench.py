@@ -297,7 +297,7 @@ def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
     """The batched uneven sweep workload (64 static droplets, L uniform over
     {128, 256, 512, 1024}, R0 = 0.2 L, T/Tc ~ U[0.6, 0.85], kappa ~ U[0, 0.6],
     A ~ U[-0.9, -0.8], FP32) stepped `steps` times, once as one batched
-    context (one launch per step, tile and CTA schedule autotuned) and once as
+    context (tile shape and schedule autotuned) and once as
     64 one-lattice contexts stepped one after another on one stream (each
     with its own autotuned tile), both from CUDA graphs and both timed with
     CUDA events on their stream.  The results of the two must be the same
@@ -344,8 +344,9 @@ def batched_vs_sequential(torch, P, steps, n=64, seed=7228):
         res_s.append(lat.measure(0, d.L / 2, d.L / 2, d.radius / 2, d.radius + SW.R_OUT_GAP)["dp"])
         lat.close()
     same = all(x == y for x, y in zip(res_b, res_s))
-    return {"workload": "%d static droplets, L in {128, 256, 512, 1024}, R0 = 0.2 L, seed %d, FP32, %d steps "
-                        "(the configured 20000 steps cut to keep the benchmark short)" % (n, seed, steps),
+    cut = "" if steps >= 20000 else " (the configured 20000 steps cut to keep the benchmark short)"
+    return {"workload": "%d static droplets, L in {128, 256, 512, 1024}, R0 = 0.2 L, seed %d, FP32, %d steps%s"
+                        % (n, seed, steps, cut),
             "nodes": nodes, "steps": steps, "batched_s": t_b, "sequential_s": t_s, "speedup": t_s / t_b,
             "batched_mlups": nodes * steps / t_b / 1e6, "sequential_mlups": nodes * steps / t_s / 1e6,
             "batched_tile": [tile, sched], "batched_launches_per_step": launches_per_step,
