@@ -265,11 +265,14 @@ int lbm_tile_config(int precision, int k, int* bx, int* by, int* threads, int* s
 int lbm_set_schedule(lbm_ctx* ctx, int tile_config, int schedule);
 /* Time every (tile configuration, schedule) pair over `steps` steps of the
  * current state (which is restored afterwards) and keep the fastest (one
- * lattice: schedules 0 and 3).  Each pair is timed as lbm_step runs it with
- * the context's current graph setting: with graphs on (lbm_use_graphs before
- * this call), the one-step schedules replay captured graphs and `steps` is
- * rounded up to whole replays.  Writes the choice and its time per step in
- * milliseconds. */
+ * lattice: schedules 0 and 3, and 4 where the lattice fits a cluster).  Each
+ * pair is timed as lbm_step runs it with the context's current graph
+ * setting: with graphs on (lbm_use_graphs before this call), the one-step
+ * schedules replay captured graphs and `steps` is rounded up to whole
+ * replays.  A pair whose bounded device waits gave up is not chosen
+ * (LBM_ETIMEOUT when no pair is left).  Writes the choice and its time per
+ * step in milliseconds.  On an error the populations, counters and schedule
+ * are put back as they were, as far as the device still allows. */
 int lbm_autotune(lbm_ctx* ctx, int steps, int* tile_config, int* schedule, double* ms_per_step);
 
 /* CUDA graphs for lbm_step: on (1) or off (0, the default).  With graphs on,

@@ -669,12 +669,13 @@ int launch_steps(lbm_ctx* c, int n) {
 // run) on first use.
 int ensure_graph(lbm_ctx* c, int parity, int level) {
     if (c->gexec[parity][level]) return LBM_OK;
-    cudaGraph_t g;
+    cudaGraph_t g = nullptr;
     CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < (2 << level); ++k) {
         cudaError_t e = launch_step(c, parity ^ (k & 1));
         if (e != cudaSuccess) {
-            cudaStreamEndCapture(c->stream, &g);
+            g = nullptr;
+            if (cudaStreamEndCapture(c->stream, &g) == cudaSuccess && g) cudaGraphDestroy(g);
             return cuda_fail(c, e, "step launch during graph capture");
         }
     }
@@ -1368,39 +1369,65 @@ int lbm_autotune(lbm_ctx* c, int steps, int* tile_config, int* schedule, double*
     // over whole graph replays (the step count rounded up to kGraphSteps),
     // after a warm-up that captures the graph
     if (c->use_graphs) steps = (steps + kGraphSteps - 1) / kGraphSteps * kGraphSteps;
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(c, cudaEventCreate(&e0));
-    CK(c, cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, LBM_ECUDA, "cudaEventCreate failed%s");
+    }
+    const int cfg0 = c->cfg, sched0 = c->sched;
     double best = 1e300;
-    int bc = c->cfg, bs = c->sched;
-    for (int k = 0; k < lbm::step_config_count(c->prec); ++k)
-        for (int s = 0; s < lbm::kMaxSched; ++s) {
+    int bc = cfg0, bs = sched0;
+    // one candidate: warm-up (which captures its graphs), then the timed
+    // steps; one whose bounded waits gave up (a launch that ended early) is
+    // not a candidate
+    std::vector<int> st(c->n);
+    auto time_one = [&](int k, int s, float* ms, bool* timed_out) -> int {
+        int r = apply_schedule(c, k, s);
+        if (!r) r = step_n(c, c->use_graphs && s < 3 ? kGraphSteps : 2);
+        if (r) return r;
+        CK(c, cudaEventRecord(e0, c->stream));
+        r = step_n(c, steps);
+        if (r) return r;
+        CK(c, cudaEventRecord(e1, c->stream));
+        CK(c, cudaEventSynchronize(e1));
+        CK(c, cudaEventElapsedTime(ms, e0, e1));
+        CK(c, cudaMemcpy(st.data(), c->d_status, c->n * sizeof(int), cudaMemcpyDeviceToHost));
+        *timed_out = std::any_of(st.begin(), st.end(), [](int v) { return (v & lbm::ST_TIMEOUT) != 0; });
+        CK(c, cudaMemset(c->d_status, 0, c->n * sizeof(int)));
+        return LBM_OK;
+    };
+    for (int k = 0; k < lbm::step_config_count(c->prec) && !rc; ++k)
+        for (int s = 0; s < lbm::kMaxSched && !rc; ++s) {
             // one lattice: the one-step launch (0), the multi-step one (3) or
             // the cluster (4, one tile configuration stands for all)
             if ((c->n == 1 && s != 0 && s < 3) || (s == 3 && !lbm::run_supported(c->prec, k))) continue;
             if (s == 4 && (k > 0 || c->n != 1 || !lbm::cluster_supported(c->prec, c->nx[0], c->ny[0]))) continue;
-            rc = apply_schedule(c, k, s);
-            if (rc) break;
-            rc = step_n(c, c->use_graphs && s < 3 ? kGraphSteps : 2);
-            if (rc) break;
-            CK(c, cudaEventRecord(e0, c->stream));
-            rc = step_n(c, steps);
-            if (rc) break;
-            CK(c, cudaEventRecord(e1, c->stream));
-            CK(c, cudaEventSynchronize(e1));
             float ms = 0;
-            CK(c, cudaEventElapsedTime(&ms, e0, e1));
-            if (ms / steps < best) { best = ms / steps; bc = k; bs = s; }
+            bool timed_out = false;
+            rc = time_one(k, s, &ms, &timed_out);
+            if (!rc && !timed_out && ms / steps < best) { best = ms / steps; bc = k; bs = s; }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc) return rc;
+    // the state as it was (after an error too: the schedule it had), then
+    // the choice
+    const std::string err = c->err;
     c->parity = parity0;
     c->steps = steps0;
     c->launches = launches0;
     for (int i = 0; i < c->n; ++i)
         CK(c, cudaMemcpy(c->h[i].pop[c->parity], snap[i].data(), snap[i].size(), cudaMemcpyHostToDevice));
     CK(c, cudaMemset(c->d_status, 0, c->n * sizeof(int)));
+    if (rc) {
+        apply_schedule(c, cfg0, sched0);
+        c->err = err;
+        return rc;
+    }
+    if (!(best < 1e300)) {
+        apply_schedule(c, cfg0, sched0);
+        return fail(c, LBM_ETIMEOUT, "every candidate's bounded device waits gave up%s");
+    }
     rc = apply_schedule(c, bc, bs);
     if (rc) return rc;
     if (tile_config) *tile_config = bc;

@@ -474,6 +474,46 @@ def test_bounded_wait_reports_timeout_and_context_survives(P, sched, other):
     lat.close()
 
 
+def test_autotune_passes_over_pairs_whose_waits_gave_up(P):
+    """Every bounded wait forced to give up: no (tile, schedule) pair of a
+    batch is left, so the autotuner reports ETIMEOUT and puts back the
+    populations, the step count and the schedule it found (here the
+    multi-step one: one launch per call); stepping afterwards gives the bits
+    of a batch that was never tuned."""
+    eos, op, rg, rl = cs_case(P)
+    shapes = [(64, 32), (48, 40)]
+    rho = [I.droplet_density(nx, ny, 8, rl, rg) for nx, ny in shapes]
+
+    def make(flags):
+        b = P.Batch([s[0] for s in shapes], [s[1] for s in shapes], P.LBM_FP32)
+        b.set_schedule(0, 3)
+        for i, r in enumerate(rho):
+            b.set_params(i, eos, op.A, op.kappa, s=S_CFG, rho_ref=rg, flags=flags)
+            b.init_density(i, r)
+        return b
+
+    b = make(P.LBM_FLAG_TEST_FORCE_TIMEOUT)
+    before = [b.read_populations(i) for i in range(len(shapes))]
+    with pytest.raises(P.LbmError) as ei:
+        b.autotune(2)
+    assert ei.value.code == -5
+    assert b.steps_done == 0
+    for i in range(len(shapes)):
+        assert np.array_equal(b.read_populations(i), before[i])
+        b.set_params(i, eos, op.A, op.kappa, s=S_CFG, rho_ref=rg, flags=0)
+    n0 = b.kernel_launches
+    b.step(7)
+    b.sync()
+    assert b.kernel_launches - n0 == 1 and b.steps_done == 7
+    ref = make(0)
+    ref.step(7)
+    ref.sync()
+    for i in range(len(shapes)):
+        assert np.array_equal(b.read_populations(i), ref.read_populations(i))
+    b.close()
+    ref.close()
+
+
 def test_symmetric_droplet_stays_bitwise_mirror_symmetric(P):
     """Rounding of the FP32 path respects the lattice mirrors: a centred drop
     stays symmetric to the last bit, so it cannot drift off its centre."""
