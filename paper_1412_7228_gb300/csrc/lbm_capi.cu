@@ -723,15 +723,23 @@ template <typename R> int init_density_t(lbm_ctx* c, int i, const R* rho, const 
     R* d_ux = ux ? scratch + N : nullptr;
     R* d_uy = uy ? scratch + 2 * N : nullptr;
     constexpr bool f32 = sizeof(R) == 4;
-    CK(c, cudaMemcpyAsync(d_rho, rho, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
-    if (ux) CK(c, cudaMemcpyAsync(d_ux, ux, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
-    if (uy) CK(c, cudaMemcpyAsync(d_uy, uy, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
     // the field is checked on the device before anything of the instance is written
     int* d_bad = reinterpret_cast<int*>(c->d_result);
     int bad = 0;
-    CK(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
-    CK(c, lbm::aux_check_init(d_rho, d_ux, d_uy, f32, static_cast<long long>(N), rmax, d_bad, c->stream));
-    CK(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    auto copy_and_check = [&]() -> int {
+        CK(c, cudaMemcpyAsync(d_rho, rho, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+        if (ux) CK(c, cudaMemcpyAsync(d_ux, ux, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+        if (uy) CK(c, cudaMemcpyAsync(d_uy, uy, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+        CK(c, lbm::aux_check_init(d_rho, d_ux, d_uy, f32, static_cast<long long>(N), rmax, d_bad, c->stream));
+        CK(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        return LBM_OK;
+    };
+    rc = copy_and_check();
+    if (rc) {   // no copy from the caller's arrays (or into `bad`) may outlive the call
+        cudaStreamSynchronize(c->stream);
+        return rc;
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     if (bad & 1) return fail(c, LBM_EINVAL, "initial density must be finite, positive and inside the EOS range%s");
     if (bad & 2) return fail(c, LBM_EINVAL, "initial velocity must be finite%s");
@@ -781,15 +789,23 @@ template <typename O> int read_fields_t(lbm_ctx* c, int i, O* rho, O* ux, O* uy,
             CK(c, cudaStreamSynchronize(c->stream));
             continue;
         }
-        for (int b = 0; b < bands; ++b) {
-            const int y0 = static_cast<int>(static_cast<long long>(ny) * b / bands);
-            const int y1 = static_cast<int>(static_cast<long long>(ny) * (b + 1) / bands);
-            const size_t off = static_cast<size_t>(y0) * nx, cnt = static_cast<size_t>(y1 - y0) * nx;
-            CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, y0, y1, scratch, f32, c->stream));
-            CK(c, cudaEventRecord(c->band_done[b], c->stream));
-            CK(c, cudaStreamWaitEvent(c->copy_stream, c->band_done[b], 0));
-            CK(c, cudaMemcpyAsync(outs[f] + off, scratch + off, cnt * sizeof(O), cudaMemcpyDeviceToHost,
-                                  c->copy_stream));
+        auto issue_bands = [&]() -> int {
+            for (int b = 0; b < bands; ++b) {
+                const int y0 = static_cast<int>(static_cast<long long>(ny) * b / bands);
+                const int y1 = static_cast<int>(static_cast<long long>(ny) * (b + 1) / bands);
+                const size_t off = static_cast<size_t>(y0) * nx, cnt = static_cast<size_t>(y1 - y0) * nx;
+                CK(c, lbm::aux_field(c->h[i], c->d_inst + i, c->parity, f, y0, y1, scratch, f32, c->stream));
+                CK(c, cudaEventRecord(c->band_done[b], c->stream));
+                CK(c, cudaStreamWaitEvent(c->copy_stream, c->band_done[b], 0));
+                CK(c, cudaMemcpyAsync(outs[f] + off, scratch + off, cnt * sizeof(O), cudaMemcpyDeviceToHost,
+                                      c->copy_stream));
+            }
+            return LBM_OK;
+        };
+        rc = issue_bands();
+        if (rc) {   // no copy into the caller's array may outlive the call
+            cudaStreamSynchronize(c->copy_stream);
+            return rc;
         }
         CK(c, cudaStreamSynchronize(c->copy_stream));   // before the next field reuses the scratch
     }
