@@ -171,7 +171,9 @@ int lbm_batch_set_viscosity(lbm_ctx* ctx, int i, int enable, double nu_gas, doub
  * there first: a density that is not finite, positive and below the EOS's
  * upper limit (4/b Carnahan-Starling, 1/b otherwise; any positive density
  * when G = 0) or a velocity that is not finite returns LBM_EINVAL and leaves
- * the instance as it was.  Synchronous. */
+ * the instance as it was.  A context of one lattice of 2^20 nodes or more
+ * takes the fields in row bands, each band checked and its populations
+ * written while the next band is copied.  Synchronous. */
 int lbm_init_density(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
 int lbm_batch_init_density(lbm_ctx* ctx, int i, const double* rho, const double* ux,
                            const double* uy);

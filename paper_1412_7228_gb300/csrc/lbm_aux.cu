@@ -3,6 +3,7 @@
 // reductions behind Laplace's law (Eq. 22) and the run statistics.
 // None of these is on the per-step path.
 #include "lbm_internal.cuh"
+#include "lbm_init.h"
 
 namespace lbm {
 namespace {
@@ -35,41 +36,43 @@ template <typename T> __device__ __forceinline__ long long at(const Inst* I, int
 // that no digit of a small difference is lost) to FP32 once and multiplies
 // by the weights in FP32 (within 1.5 ulp of the correctly rounded value, and
 // two FP64 operations per node instead of seven: GB300's FP64 pipe would
-// otherwise bound the initialisation).
+// otherwise bound the initialisation).  Rows [y0, y1) of the field; rho,
+// ux and uy index the whole field.
 template <typename T, bool REST, typename R>
 __global__ void k_init(const Inst* __restrict__ I, const R* __restrict__ rho, const R* __restrict__ ux,
-                       const R* __restrict__ uy, int parity) {
+                       const R* __restrict__ uy, int parity, int y0, int y1) {
     const int nx = I->nx, ny = I->ny;
     T* p = popk<T>(I, parity);
     const double rr = static_cast<double>(phys<T>(I).rho_ref);
-    LBM_FOR_NODES(nx, ny) {
-        const long long i = static_cast<long long>(y) * nx + x;
-        const double r = rho[i], u = !REST && ux ? double(ux[i]) : 0.0, v = !REST && uy ? double(uy[i]) : 0.0;
-        const double u2 = u * u + v * v;
-        // at rest: the three weights' products
-        const double d = r - rr;
-        T rest[3];
-        if constexpr (sizeof(T) == 4) {
-            const float df = static_cast<float>(d);
-            rest[0] = __fmul_rn(4.0f / 9.0f, df);
-            rest[1] = __fmul_rn(1.0f / 9.0f, df);
-            rest[2] = __fmul_rn(1.0f / 36.0f, df);
-        } else {
-            rest[0] = tw(0) * d;
-            rest[1] = tw(1) * d;
-            rest[2] = tw(5) * d;
-        }
+    for (int y = y0 + static_cast<int>(blockIdx.y); y < y1; y += gridDim.y)
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+            const long long i = static_cast<long long>(y) * nx + x;
+            const double r = rho[i], u = !REST && ux ? double(ux[i]) : 0.0, v = !REST && uy ? double(uy[i]) : 0.0;
+            const double u2 = u * u + v * v;
+            // at rest: the three weights' products
+            const double d = r - rr;
+            T rest[3];
+            if constexpr (sizeof(T) == 4) {
+                const float df = static_cast<float>(d);
+                rest[0] = __fmul_rn(4.0f / 9.0f, df);
+                rest[1] = __fmul_rn(1.0f / 9.0f, df);
+                rest[2] = __fmul_rn(1.0f / 36.0f, df);
+            } else {
+                rest[0] = tw(0) * d;
+                rest[1] = tw(1) * d;
+                rest[2] = tw(5) * d;
+            }
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            const double eu = cx(a) * u + cy(a) * v;
-            // textbook second-order equilibrium, minus t_a rho_ref
-            const double dev = REST ? 0.0 : tw(a) * ((r - rr) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * u2));
-            int xs = x - cx(a), ys = y - cy(a);
-            xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-            ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-            p[at<T>(I, a, xs, ys)] = REST ? rest[a == 0 ? 0 : (a < 5 ? 1 : 2)] : static_cast<T>(dev);
+            for (int a = 0; a < 9; ++a) {
+                const double eu = cx(a) * u + cy(a) * v;
+                // textbook second-order equilibrium, minus t_a rho_ref
+                const double dev = REST ? 0.0 : tw(a) * ((r - rr) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * u2));
+                int xs = x - cx(a), ys = y - cy(a);
+                xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+                ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+                p[at<T>(I, a, xs, ys)] = REST ? rest[a == 0 ? 0 : (a < 5 ? 1 : 2)] : static_cast<T>(dev);
+            }
         }
-    }
 }
 
 // The checks of an initial field, on the device: bit 1 of *bad when a
@@ -446,26 +449,31 @@ cudaError_t aux_fp64_fma_rate(int iters, cudaStream_t st, double* flops_per_s, d
 }
 
 template <typename R>
-cudaError_t init_t(const Inst& h, const Inst* d, const R* rho, const R* ux, const R* uy, int parity,
-                   cudaStream_t st) {
-    const dim3 g = grid_2d(h.nx, h.ny);
+cudaError_t init_rows_t(const Inst& h, const Inst* d, const R* rho, const R* ux, const R* uy, int parity, int y0,
+                        int y1, cudaStream_t st) {
+    const dim3 g = grid_2d(h.nx, y1 - y0);
     const bool rest = !ux && !uy;
-    if (h.prec == LBM_FP32 && rest) k_init<float, true, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
-    else if (h.prec == LBM_FP32) k_init<float, false, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
-    else if (rest) k_init<double, true, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
-    else k_init<double, false, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return aux_fill_ghosts(h, d, parity, st);
+    if (h.prec == LBM_FP32 && rest) k_init<float, true, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity, y0, y1);
+    else if (h.prec == LBM_FP32) k_init<float, false, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity, y0, y1);
+    else if (rest) k_init<double, true, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity, y0, y1);
+    else k_init<double, false, R><<<g, kThreads, 0, st>>>(d, rho, ux, uy, parity, y0, y1);
+    return cudaGetLastError();
 }
 
 cudaError_t aux_init(const Inst& h, const Inst* d, const void* rho, const void* ux, const void* uy, bool f32,
                      int parity, cudaStream_t st) {
+    const cudaError_t e = aux_init_rows(h, d, rho, ux, uy, f32, parity, 0, h.ny, st);
+    return e != cudaSuccess ? e : aux_fill_ghosts(h, d, parity, st);
+}
+
+cudaError_t aux_init_rows(const Inst& h, const Inst* d, const void* rho, const void* ux, const void* uy, bool f32,
+                          int parity, int y0, int y1, cudaStream_t st) {
+    if (y0 < 0 || y1 > h.ny || y0 >= y1) return cudaErrorInvalidValue;
     if (f32)
-        return init_t(h, d, static_cast<const float*>(rho), static_cast<const float*>(ux),
-                      static_cast<const float*>(uy), parity, st);
-    return init_t(h, d, static_cast<const double*>(rho), static_cast<const double*>(ux),
-                  static_cast<const double*>(uy), parity, st);
+        return init_rows_t(h, d, static_cast<const float*>(rho), static_cast<const float*>(ux),
+                           static_cast<const float*>(uy), parity, y0, y1, st);
+    return init_rows_t(h, d, static_cast<const double*>(rho), static_cast<const double*>(ux),
+                       static_cast<const double*>(uy), parity, y0, y1, st);
 }
 
 cudaError_t aux_check_init(const void* rho, const void* ux, const void* uy, bool f32, long long N, double rho_max,

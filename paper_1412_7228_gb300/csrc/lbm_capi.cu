@@ -14,6 +14,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "lbm_eos_host.h"
+#include "lbm_init.h"
 #include "lbm_internal.cuh"
 
 using lbm::Inst;
@@ -707,6 +708,34 @@ int valid_params(const lbm_eos* eos, double A, double kappa, double G, const dou
 // =========================================================================
 namespace {
 // Initial state from host fields of R (double, or float widened exactly).
+// Row bands of a field moved between host and device: a lattice of 2^20
+// nodes or more in kReadBands bands (each band's copy overlapping another
+// band's kernel), a smaller one whole.
+int field_bands(const lbm_ctx* c, int i) {
+    const size_t N = static_cast<size_t>(c->nx[i]) * c->ny[i];
+    return N >= kReadBandMin && c->ny[i] >= kReadBands ? kReadBands : 1;
+}
+
+// The second stream of the banded copies and its per-band events, created
+// once, whole or not at all.
+int ensure_copy_stream(lbm_ctx* c) {
+    if (c->copy_stream) return LBM_OK;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[kReadBands] = {};
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int b = 0; b < kReadBands && e == cudaSuccess; ++b)
+        e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (auto x : ev)
+            if (x) cudaEventDestroy(x);
+        if (cs) cudaStreamDestroy(cs);
+        return cuda_fail(c, e, "copy stream of the banded field transfers");
+    }
+    c->copy_stream = cs;
+    std::copy(ev, ev + kReadBands, c->band_done);
+    return LBM_OK;
+}
+
 template <typename R> int init_density_t(lbm_ctx* c, int i, const R* rho, const R* ux, const R* uy) {
     int rc = check_idx(c, i);
     if (rc) return rc;
@@ -723,27 +752,63 @@ template <typename R> int init_density_t(lbm_ctx* c, int i, const R* rho, const 
     R* d_ux = ux ? scratch + N : nullptr;
     R* d_uy = uy ? scratch + 2 * N : nullptr;
     constexpr bool f32 = sizeof(R) == 4;
-    // the field is checked on the device before anything of the instance is written
+    // the field is checked on the device before anything of the instance's
+    // current time level is written.  One lattice of 2^20 nodes or more: the
+    // field arrives in row bands on the copy stream, each band checked and
+    // its equilibrium written into the other time level (which the next step
+    // overwrites whole) while the next band is in flight; that level becomes
+    // the current one once the whole field has passed.
     int* d_bad = reinterpret_cast<int*>(c->d_result);
     int bad = 0;
+    const int bands = c->n == 1 ? field_bands(c, i) : 1;
+    const int level = bands > 1 ? c->parity ^ 1 : c->parity;
+    if (bands > 1 && (rc = ensure_copy_stream(c))) return rc;
     auto copy_and_check = [&]() -> int {
-        CK(c, cudaMemcpyAsync(d_rho, rho, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
-        if (ux) CK(c, cudaMemcpyAsync(d_ux, ux, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
-        if (uy) CK(c, cudaMemcpyAsync(d_uy, uy, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
         CK(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
-        CK(c, lbm::aux_check_init(d_rho, d_ux, d_uy, f32, static_cast<long long>(N), rmax, d_bad, c->stream));
+        if (bands == 1) {
+            CK(c, cudaMemcpyAsync(d_rho, rho, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+            if (ux) CK(c, cudaMemcpyAsync(d_ux, ux, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+            if (uy) CK(c, cudaMemcpyAsync(d_uy, uy, N * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+            CK(c, lbm::aux_check_init(d_rho, d_ux, d_uy, f32, static_cast<long long>(N), rmax, d_bad, c->stream));
+        } else {
+            const int nx = c->nx[i], ny = c->ny[i];
+            for (int b = 0; b < bands; ++b) {
+                const int y0 = static_cast<int>(static_cast<long long>(ny) * b / bands);
+                const int y1 = static_cast<int>(static_cast<long long>(ny) * (b + 1) / bands);
+                const size_t off = static_cast<size_t>(y0) * nx, cnt = static_cast<size_t>(y1 - y0) * nx;
+                CK(c, cudaMemcpyAsync(d_rho + off, rho + off, cnt * sizeof(R), cudaMemcpyHostToDevice, c->copy_stream));
+                if (ux)
+                    CK(c, cudaMemcpyAsync(d_ux + off, ux + off, cnt * sizeof(R), cudaMemcpyHostToDevice,
+                                          c->copy_stream));
+                if (uy)
+                    CK(c, cudaMemcpyAsync(d_uy + off, uy + off, cnt * sizeof(R), cudaMemcpyHostToDevice,
+                                          c->copy_stream));
+                CK(c, cudaEventRecord(c->band_done[b], c->copy_stream));
+                CK(c, cudaStreamWaitEvent(c->stream, c->band_done[b], 0));
+                CK(c, lbm::aux_check_init(d_rho + off, d_ux ? d_ux + off : nullptr, d_uy ? d_uy + off : nullptr, f32,
+                                          static_cast<long long>(cnt), rmax, d_bad, c->stream));
+                CK(c, lbm::aux_init_rows(c->h[i], c->d_inst + i, d_rho, d_ux, d_uy, f32, level, y0, y1, c->stream));
+            }
+        }
         CK(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         return LBM_OK;
     };
     rc = copy_and_check();
     if (rc) {   // no copy from the caller's arrays (or into `bad`) may outlive the call
+        if (bands > 1) cudaStreamSynchronize(c->copy_stream);
         cudaStreamSynchronize(c->stream);
         return rc;
     }
+    // the stream waited for every band's copy: all of them have landed
     CK(c, cudaStreamSynchronize(c->stream));
     if (bad & 1) return fail(c, LBM_EINVAL, "initial density must be finite, positive and inside the EOS range%s");
     if (bad & 2) return fail(c, LBM_EINVAL, "initial velocity must be finite%s");
-    CK(c, lbm::aux_init(c->h[i], c->d_inst + i, d_rho, d_ux, d_uy, f32, c->parity, c->stream));
+    if (bands == 1) {
+        CK(c, lbm::aux_init(c->h[i], c->d_inst + i, d_rho, d_ux, d_uy, f32, c->parity, c->stream));
+    } else {
+        CK(c, lbm::aux_fill_ghosts(c->h[i], c->d_inst + i, level, c->stream));
+        c->parity = level;
+    }
     CK(c, cudaMemsetAsync(c->d_status + i, 0, sizeof(int), c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     c->inited[i] = 1;
@@ -762,22 +827,8 @@ template <typename O> int read_fields_t(lbm_ctx* c, int i, O* rho, O* ux, O* uy,
     const int nx = c->nx[i], ny = c->ny[i];
     const size_t N = static_cast<size_t>(nx) * ny;
     // a large lattice in row bands: band b's copy to the host overlaps band b + 1's kernel
-    const int bands = N >= kReadBandMin && ny >= kReadBands ? kReadBands : 1;
-    if (bands > 1 && !c->copy_stream) {   // created once, whole or not at all
-        cudaStream_t cs = nullptr;
-        cudaEvent_t ev[kReadBands] = {};
-        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-        for (int b = 0; b < kReadBands && e == cudaSuccess; ++b)
-            e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            for (auto x : ev)
-                if (x) cudaEventDestroy(x);
-            if (cs) cudaStreamDestroy(cs);
-            return cuda_fail(c, e, "read-back copy stream");
-        }
-        c->copy_stream = cs;
-        std::copy(ev, ev + kReadBands, c->band_done);
-    }
+    const int bands = field_bands(c, i);
+    if (bands > 1 && (rc = ensure_copy_stream(c))) return rc;
     O* outs[4] = {rho, ux, uy, psi};
     O* const scratch = reinterpret_cast<O*>(c->d_scratch);
     constexpr bool f32 = sizeof(O) == 4;

@@ -174,6 +174,55 @@ def test_banded_read_back_of_a_large_lattice_matches_the_oracle_macro(P, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
+def test_banded_initialisation_refuses_a_bad_band_and_keeps_the_state(P, prec):
+    """A lattice of over 2^20 nodes takes its initial field in row bands,
+    each band checked and written while the next is still being copied: a
+    field with one bad value in its last band (or one bad velocity) is
+    refused and leaves the populations, the step count and the steps that
+    follow as they were; a good field gives, bit for bit, the populations of
+    the whole-field path (which an instance of a batch takes)."""
+    eos, op, rg, rl = _cs(P)
+    nx, ny = 1040, 1030
+    rho0 = I.droplet_density(nx, ny, 200, rl, rg)
+    ux = 0.01 * np.sin(np.arange(nx * ny).reshape(ny, nx) * 0.003)
+    lat = P.Lattice(nx, ny, prec)
+    lat.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=rg)
+    lat.init_density(rho0)
+    lat.step(3)
+    keep = lat.read_populations()
+    bad = rho0.copy()
+    bad[ny - 2, 17] = np.nan
+    vbad = ux.copy()
+    vbad[5, 3] = np.inf
+    for kw in (dict(rho=bad), dict(rho=rho0, ux=vbad)):
+        with pytest.raises(P.LbmError) as ei:
+            lat.init_density(**kw)
+        assert ei.value.code == -1
+        assert lat.steps_done == 3 and np.array_equal(lat.read_populations(), keep)
+    lat.step(2)
+    ref = P.Lattice(nx, ny, prec)
+    ref.set_params(eos, -0.85, 0.3, s=S_CFG, rho_ref=rg)
+    ref.init_density(rho0)
+    ref.step(5)
+    assert np.array_equal(lat.read_populations(), ref.read_populations())
+    ref.close()
+    b = P.Batch([nx, 16], [ny, 16], prec)
+    for i in range(2):
+        b.set_params(i, eos, -0.85, 0.3, s=S_CFG, rho_ref=rg)
+    b.init_density(1, I.droplet_density(16, 16, 4, rl, rg))
+    for kw in (dict(), dict(ux=ux)):
+        lat.init_density(rho0, **kw)
+        b.init_density(0, rho0, **kw)
+        assert lat.steps_done == 0
+        assert np.array_equal(lat.read_populations(), b.read_populations(0))
+    lat.step(4)
+    b.step(4)
+    assert np.array_equal(lat.read_populations(), b.read_populations(0))
+    lat.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
 def test_fp32_field_interface(P, prec):
     """The FP32 entry points move half the bytes and mean the same: a float32
     initial field gives the populations of its exact float64 widening, every
