@@ -124,6 +124,17 @@ int lbm_fp64_fma_rate(int iters, void* stream, double* flops_per_s, double* seco
 size_t lbm_required_bytes(int nx, int ny, int precision);
 size_t lbm_batch_required_bytes(int n, const int* nx, const int* ny, int precision);
 
+/* How the multi-step schedule (schedule 3 of lbm_set_schedule) groups a
+ * batch of these lattices into launches: instances taken largest first
+ * (index order among equal sizes) into as few chunks as 32 instances and
+ * 80 MiB of populations (both time levels) per chunk allow, an instance
+ * larger than that alone, with the bytes spread evenly over the chunks.
+ * Writes the chunk of instance i to chunk_of[i] (caller-owned, n ints;
+ * chunks numbered in launch order) and returns the number of chunks.  Host
+ * arithmetic only: needs no device.  LBM_EINVAL for the shapes
+ * lbm_batch_required_bytes refuses or a NULL chunk_of. */
+int lbm_run_chunk_plan(int n, const int* nx, const int* ny, int precision, int* chunk_of);
+
 /* Create a context of one nx x ny periodic lattice (lbm_create) or of n
  * independent lattices (lbm_batch_create) in the given precision; nx and ny
  * in [2, 2^20].  dev_buf: caller-owned device memory of at least the required

@@ -411,57 +411,71 @@ int build_chunks(lbm_ctx* c, std::vector<lbm::BatchArgs<T>> (&out)[2], const std
     return LBM_OK;
 }
 
-// Argument blocks of the multi-step launches: instances largest first, cut
-// into as few chunks as kRunMax instances per chunk and kRunChunkBytes of
-// populations (both time levels) per chunk allow (an instance larger than
-// that is a chunk of its own), with the bytes spread evenly over the chunks;
-// a chunk steps its instances through all the steps of one lbm_step call in
+// The chunks of the multi-step launches over instances of bytes[i] bytes of
+// populations (both time levels): instances largest first (index order
+// among equal sizes, so that a chunk holds lattices of one size and its
+// tiles per step stay even), cut into as few chunks as kRunMax instances per
+// chunk and kRunChunkBytes per chunk allow (an instance larger than that is
+// a chunk of its own), with the bytes spread evenly over the chunks.  A
+// chunk steps its instances through all the steps of one lbm_step call in
 // one launch (instances are independent), so a chunk that fits in L2 (129 MB
 // on GB300) keeps its populations there from step to step.  Even chunks
 // matter: a last chunk of a few instances has too few tiles per step for
 // the resident CTAs, which then wait on its step-to-step dependencies (60
 // droplets of 256^2 in chunks of 13 and a last one of 8: 69.7 G updates/s;
-// in four chunks of 15: 75.7).
+// in four chunks of 15: 75.7).  Host arithmetic only.
 constexpr size_t kRunChunkBytes = static_cast<size_t>(LBM_RUN_CHUNK_MB) << 20;
+std::vector<std::vector<int>> plan_run_chunks(const std::vector<size_t>& bytes) {
+    const int n = static_cast<int>(bytes.size());
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bytes[x] > bytes[y]; });
+    auto bytes_of = [&](int j) { return bytes[order[j]]; };
+    // the chunk count: as many as filling each chunk up to the limits needs
+    size_t left = 0;
+    int chunks = 0;
+    for (int c0 = 0, m = 0; c0 < n; c0 += m, ++chunks) {
+        size_t sum = 0;
+        for (m = 0; c0 + m < n && m < lbm::kRunMax; ++m) {
+            const size_t b = bytes_of(c0 + m);
+            if (m > 0 && sum + b > kRunChunkBytes) break;
+            sum += b;
+        }
+        left += sum;
+    }
+    std::vector<std::vector<int>> plan;
+    for (int c0 = 0, m = 0; c0 < n; c0 += m, --chunks) {
+        // this chunk's share of what is left, cut at the instance nearest to it
+        const size_t target = left / static_cast<size_t>(std::max(chunks, 1));
+        size_t sum = 0;
+        for (m = 0; c0 + m < n && m < lbm::kRunMax; ++m) {
+            const size_t b = bytes_of(c0 + m);
+            if (m > 0 && (sum + b > kRunChunkBytes || sum + b / 2 > target)) break;
+            sum += b;
+        }
+        left -= sum;
+        plan.emplace_back(order.begin() + c0, order.begin() + c0 + m);
+    }
+    return plan;
+}
+
+// Argument blocks of the multi-step launches, one per chunk of
+// plan_run_chunks.
 template <typename T>
 int build_run_chunks(lbm_ctx* c, std::vector<lbm::RunArgs<T>>& out, const std::vector<int>& tx,
                      const std::vector<int>& cnt) {
     int* done = reinterpret_cast<int*>(c->d_run + 16);
-    // instances largest first (index order among equal sizes), so that a
-    // chunk holds lattices of one size: its tiles per step stay even
-    std::vector<int> order(c->n);
-    for (int i = 0; i < c->n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return c->h[x].plane > c->h[y].plane; });
-    auto bytes_of = [&](int j) { return 2 * 9 * static_cast<size_t>(c->h[order[j]].plane) * c->esz; };
-    // the chunk count: as many as filling each chunk up to the limits needs
-    size_t left = 0;
-    int chunks = 0;
-    for (int c0 = 0, m = 0; c0 < c->n; c0 += m, ++chunks) {
-        size_t bytes = 0;
-        for (m = 0; c0 + m < c->n && m < lbm::kRunMax; ++m) {
-            const size_t b = bytes_of(c0 + m);
-            if (m > 0 && bytes + b > kRunChunkBytes) break;
-            bytes += b;
-        }
-        left += bytes;
-    }
+    std::vector<size_t> bytes(c->n);
+    for (int i = 0; i < c->n; ++i) bytes[i] = 2 * 9 * static_cast<size_t>(c->h[i].plane) * c->esz;
     int tile0 = 0;
-    for (int c0 = 0, m = 0; c0 < c->n; c0 += m, --chunks) {
-        // this chunk's share of what is left, cut at the instance nearest to it
-        const size_t target = left / static_cast<size_t>(std::max(chunks, 1));
-        size_t bytes = 0;
-        for (m = 0; c0 + m < c->n && m < lbm::kRunMax; ++m) {
-            const size_t b = bytes_of(c0 + m);
-            if (m > 0 && (bytes + b > kRunChunkBytes || bytes + b / 2 > target)) break;
-            bytes += b;
-        }
-        left -= bytes;
+    for (const std::vector<int>& chunk : plan_run_chunks(bytes)) {
+        const int m = static_cast<int>(chunk.size());
         lbm::RunArgs<T> a;
         std::memset(&a, 0, sizeof a);
         a.n = m;
         int first = 0;
         for (int k = 0; k < m; ++k) {
-            const int i = order[c0 + k];
+            const int i = chunk[k];
             const Inst& I = c->h[i];
             a.inst[k] = i;
             a.tiles_x[k] = tx[i];
@@ -991,6 +1005,17 @@ size_t lbm_batch_required_bytes(int n, const int* nx, const int* ny, int precisi
 }
 
 size_t lbm_required_bytes(int nx, int ny, int precision) { return lbm_batch_required_bytes(1, &nx, &ny, precision); }
+
+int lbm_run_chunk_plan(int n, const int* nx, const int* ny, int precision, int* chunk_of) {
+    if (!valid_shape(n, nx, ny, precision) || !chunk_of) return LBM_EINVAL;
+    std::vector<size_t> bytes(n);
+    for (int i = 0; i < n; ++i)
+        bytes[i] = 2 * 9 * static_cast<size_t>(pitch_of(nx[i], precision)) * (ny[i] + 2 * lbm::GY) * esize(precision);
+    const std::vector<std::vector<int>> plan = plan_run_chunks(bytes);
+    for (size_t k = 0; k < plan.size(); ++k)
+        for (int i : plan[k]) chunk_of[i] = static_cast<int>(k);
+    return static_cast<int>(plan.size());
+}
 
 int lbm_batch_create(lbm_ctx** out, int n, const int* nx, const int* ny, int precision, void* dev_buf,
                      size_t buf_bytes, void* stream) {

@@ -31,7 +31,7 @@ _CODES = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA", LBM_EU
 EXPORTS = [
     "lbm_eos_pressure", "lbm_eos_critical", "lbm_eos_maxwell", "lbm_laplace_fit", "lbm_fp64_math_check",
     "lbm_fp64_fma_rate",
-    "lbm_required_bytes", "lbm_batch_required_bytes", "lbm_create", "lbm_batch_create", "lbm_destroy",
+    "lbm_required_bytes", "lbm_batch_required_bytes", "lbm_run_chunk_plan", "lbm_create", "lbm_batch_create", "lbm_destroy",
     "lbm_set_params", "lbm_batch_set_params", "lbm_set_viscosity", "lbm_batch_set_viscosity",
     "lbm_init_density", "lbm_batch_init_density", "lbm_init_density_f32", "lbm_batch_init_density_f32",
     "lbm_step", "lbm_sync", "lbm_status", "lbm_clear_status",
@@ -99,6 +99,7 @@ def lib():
         "lbm_laplace_fit": ([ctypes.c_int, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
         "lbm_required_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
         "lbm_batch_required_bytes": ([ctypes.c_int, _ip, _ip, ctypes.c_int], ctypes.c_size_t),
+        "lbm_run_chunk_plan": ([ctypes.c_int, _ip, _ip, ctypes.c_int, _ip], ctypes.c_int),
         "lbm_create": ([ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp],
                        ctypes.c_int),
         "lbm_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip, ctypes.c_int, _vp, ctypes.c_size_t, _vp],
@@ -265,6 +266,18 @@ def lbm_batch_required_bytes(nx: Sequence[int], ny: Sequence[int], precision: in
     ax = (ctypes.c_int * n)(*nx)
     ay = (ctypes.c_int * n)(*ny)
     return int(lib().lbm_batch_required_bytes(n, ax, ay, precision))
+
+
+def lbm_run_chunk_plan(nx: Sequence[int], ny: Sequence[int], precision: int) -> list:
+    """The chunk (launch) of each lattice under the multi-step schedule."""
+    n = len(nx)
+    ax = (ctypes.c_int * n)(*nx)
+    ay = (ctypes.c_int * n)(*ny)
+    out = (ctypes.c_int * n)()
+    rc = lib().lbm_run_chunk_plan(n, ax, ay, precision, out)
+    if rc < 0:
+        raise LbmError(rc, "invalid lattice shapes")
+    return list(out)
 
 
 def lbm_tile_configs(precision: int):
