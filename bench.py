@@ -617,11 +617,14 @@ def run_ours(args):
         lat.read_fields(which=("rho",), out={"rho": out_rho}, dtype=fdt)
         t_e2e = time.perf_counter() - t0
         lat.close()
+        # the whole job: every replica's updates over the slowest replica's time,
+        # and every replica's copies
+        t_e2e = max_over_ranks(t_e2e, dist, "cuda")
         esz = np.dtype(fdt).itemsize
-        e2e = {"value": N * args.steps / t_e2e / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": esz * N / args.steps, "d2h_bytes_per_step": esz * N / args.steps,
+        e2e = {"value": whole_job_mlups(ws, N, args.steps, t_e2e), "unit": "MLUPS",
+               "h2d_bytes_per_step": ws * esz * N / args.steps, "d2h_bytes_per_step": ws * esz * N / args.steps,
                "what": "lbm_init_density%s from pinned host rho, lbm_step(K), lbm_read_fields%s(rho) to pinned host memory"
-                       % (("_f32", "_f32") if esz == 4 else ("", ""))}
+                       % (("_f32", "_f32") if esz == 4 else ("", "")) + (", on each of %d ranks" % ws if ws > 1 else "")}
 
     # ---- the plain-method workload in full: 64^2 droplet, 10^4 steps --------
     plain = None
@@ -639,7 +642,7 @@ def run_ours(args):
         batched = batched_vs_sequential(torch, P, args.sweep_steps)
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu:   # the CPU baseline: one process, N = 1 only
         cn = args.cpu_n
         m, dt = cpu_oracle_mlups(cn, cn, args.cpu_steps)
         cpu = {"value": m, "unit": "MLUPS", "cores": 1, "kind": "oracle",
