@@ -105,3 +105,48 @@ def test_context_calls_refuse_a_null_context(liblbm):
     assert L.lbm_read_fields_f32(None, None, None, None, None) == E
     assert L.lbm_batch_init_density_f32(None, 0, None, None, None) == E
     assert L.lbm_batch_read_fields_f32(None, 0, None, None, None, None) == E
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "lbm.h"
+
+int main(void) {
+    lbm_eos eos = {LBM_EOS_CS, 1.0, 4.0, 1.0, 1.0, 0.0, 0.0, 0.0};
+    double rho_c, T_c, p_c;
+    int nx[3] = {256, 256, 4096}, ny[3] = {256, 256, 4096}, chunk_of[3];
+    int bx, by, threads, stages, chunks;
+    if (lbm_eos_critical(&eos, &rho_c, &T_c, &p_c) != LBM_OK) return 1;
+    if (lbm_tile_config(LBM_FP32, 0, &bx, &by, &threads, &stages) != LBM_OK) return 2;
+    chunks = lbm_run_chunk_plan(3, nx, ny, LBM_FP32, chunk_of);
+    printf("%.9f %.9f %d %d %d %d %d %zu %d %d %d %d\n", rho_c, T_c, bx, by, threads, stages,
+           lbm_bytes_per_update(LBM_FP32), lbm_required_bytes(1, 64, LBM_FP32), chunks, chunk_of[0],
+           chunk_of[1], chunk_of[2]);
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_host_calls_link_from_c(liblbm, tmp_path):
+    """include/lbm.h compiles as strict C99 (no C++ in the boundary), and a C
+    program links against liblbm.so and makes the host-only calls."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_lbm.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_lbm"
+    lib_dir = os.path.dirname(liblbm._name)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", lib_dir, "-llbm", "-Wl,-rpath," + lib_dir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    v = out.stdout.split()
+    assert abs(float(v[0]) - 0.130444) < 1e-5 and abs(float(v[1]) - 0.0943287) < 1e-6   # R15
+    assert v[2:6] == ["128", "16", "512", "1"] and v[6] == "72"
+    assert v[7] == "0"                                     # nx = 1 is refused
+    assert v[8:] == ["2", "1", "1", "0"]                    # the 4096^2 lattice alone, first
