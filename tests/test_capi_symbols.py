@@ -150,3 +150,22 @@ def test_header_is_plain_c_and_host_calls_link_from_c(liblbm, tmp_path):
     assert v[2:6] == ["128", "16", "512", "1"] and v[6] == "72"
     assert v[7] == "0"                                     # nx = 1 is refused
     assert v[8:] == ["2", "1", "1", "0"]                    # the 4096^2 lattice alone, first
+
+
+def test_laplace_fit_agrees_with_the_oracle_and_refuses_degenerate_input(liblbm):
+    """The library's FP64 least squares of Eq. 22 against the oracle's on
+    noisy points; fewer than two points, a non-positive radius or a single
+    radius (no slope) are refused."""
+    import numpy as np
+    from oracle import analysis as An
+    import paper_1412_7228_gb300 as P
+    rng = np.random.default_rng(5)
+    R = np.array([16.1, 28.1, 38.8, 49.3, 59.6])
+    dp = 0.012 / R + 7e-6 + rng.normal(0.0, 2e-6, R.size)
+    s, c, r2 = P.lbm_laplace_fit(list(dp), list(R))
+    so, co, r2o = An.laplace_fit(list(dp), list(R))
+    assert abs(s / so - 1) < 1e-12 and abs(c - co) < 1e-15 and abs(r2 - r2o) < 1e-12 and 0.99 < r2 < 1
+    for dps, Rs in (([1e-3], [10.0]), ([1e-3, 2e-3], [10.0, 0.0]), ([1e-3, 2e-3], [10.0, -5.0]),
+                    ([1e-3, 2e-3, 3e-3], [12.0, 12.0, 12.0])):
+        with pytest.raises(P.LbmError):
+            P.lbm_laplace_fit(dps, Rs)
